@@ -1,0 +1,167 @@
+/*
+ * kdfmm -- GB300 (sm_103a) kd-tree fast multipole gravity: C ABI.
+ *
+ * One gravitational force evaluation for N softened particles by the kd-tree
+ * FMM analysed in Potashov & Yudin, arXiv 2502.01496 (Sec. 2 and Sec. 4):
+ *   tree build     -- centre-of-mass cuts across the longest axis (Sec. 2);
+ *   moments        -- M, centre of mass, size s, h_max, quadrupole Q (Eq. 7);
+ *   walk           -- for every leaf only, opening criteria Eq. 4 and Eq. 5;
+ *   M2L / L2P      -- Eq. 6 and its second-order Taylor expansion Eq. 8;
+ *   P2P            -- softened direct sums over opened leaves (Eq. 13);
+ *   assembly       -- a = a_short + a_long (Eq. 3), in caller order;
+ *   total momentum -- sum_i m_i a_i, the paper's measure of non-conservation
+ *                     (Sec. 4, Eq. 30).
+ *
+ * Conventions shared by every entry point:
+ *   - Array arguments are DEVICE pointers to memory the caller owns, unless a
+ *     parameter says "host".  Positions are N x 3 row-major float64
+ *     (x0 y0 z0 x1 ...); masses, smoothing lengths and potentials are N float64.
+ *     Outputs are written in the caller's particle order.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued on it; a call returns once its work is enqueued, except
+ *     where a parameter says the call synchronises.
+ *   - Every call returns a status code (KDFMM_OK or a negative KDFMM_ERR_*);
+ *     nothing throws across the ABI.  kdfmm_last_error() returns a message for
+ *     the calling thread's last failure.  After KDFMM_ERR_CUDA the handle must
+ *     be destroyed.
+ *   - G = 1 (Sec. 2, Eq. 1).
+ */
+#ifndef KDFMM_H
+#define KDFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KDFMM_OK 0
+#define KDFMM_ERR_INVALID_ARG (-1)  /* bad size, parameter or pointer */
+#define KDFMM_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define KDFMM_ERR_OOM (-3)          /* device allocation failed */
+#define KDFMM_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up */
+#define KDFMM_ERR_CAPACITY (-5)     /* an internal list outgrew its capacity */
+#define KDFMM_ERR_NONFINITE (-6)    /* NaN/Inf position, non-positive mass or h */
+#define KDFMM_ERR_INTERNAL (-7)     /* a device-side consistency check failed */
+
+#define KDFMM_SOFT_PLUMMER 0        /* a = -m d / (d^2 + eps^2)^(3/2); h_i = eps */
+#define KDFMM_SOFT_M4 1             /* M4 cubic-spline kernel, per-particle h (Eq. 13) */
+
+#define KDFMM_FP64 0                /* all force arithmetic in float64 */
+#define KDFMM_MIXED 1               /* float32 P2P/M2L/L2P with compensated sums */
+
+#define KDFMM_MAX_LEAF 32           /* largest supported n_leaf */
+
+typedef struct kdfmm_tree_s* kdfmm_tree;   /* opaque, library-owned */
+
+typedef struct {
+    double theta;        /* opening parameter of Eq. 4, 0 <= theta <= 1 */
+    double eps;          /* Plummer softening length (soft_kind 0); also h_i then */
+    double r_kern;       /* kernel support radius in units of h in Eq. 5 (2 for M4) */
+    int32_t n_leaf;      /* a cell holding more particles is split (Sec. 2); 1..32 */
+    int32_t soft_kind;   /* KDFMM_SOFT_PLUMMER or KDFMM_SOFT_M4 */
+    int32_t precision;   /* KDFMM_FP64 or KDFMM_MIXED */
+    int32_t reserved;    /* must be 0 */
+} kdfmm_params;
+
+/* Statistics of the last build / evaluation (kdfmm_tree_stats indices). */
+#define KDFMM_STAT_N 0
+#define KDFMM_STAT_NCELLS 1
+#define KDFMM_STAT_NLEAVES 2
+#define KDFMM_STAT_DEPTH 3        /* deepest cell level (root = 0) */
+#define KDFMM_STAT_NFAR 4         /* M2L pairs (sum of far-list lengths) */
+#define KDFMM_STAT_NNEAR 5        /* near-list entries (leaf pairs) */
+#define KDFMM_STAT_NP2P 6         /* particle-particle interactions, self excluded */
+#define KDFMM_STAT_NFALLBACK 7    /* degenerate cuts split by position */
+#define KDFMM_STAT_NEXACT 8       /* opening decisions settled in float64 */
+#define KDFMM_STAT_LAUNCHES 9     /* kernels launched since the handle was created */
+#define KDFMM_NSTATS 10
+
+/* Phases timed by kdfmm_tree_timing (milliseconds of the most recent call). */
+#define KDFMM_PHASE_BUILD 0       /* kdfmm_tree_build: tree + moments */
+#define KDFMM_PHASE_WALK 1        /* interaction lists */
+#define KDFMM_PHASE_M2L 2
+#define KDFMM_PHASE_P2P 3         /* P2P + L2P + assembly */
+#define KDFMM_NPHASES 4
+
+/* Creates an empty handle on the current CUDA device.  Buffers are allocated
+ * by the first build and reused by later builds of no more particles.
+ * `out` is a host pointer that receives the handle. */
+int kdfmm_tree_create(kdfmm_tree* out);
+
+/* Releases the handle and its device memory (synchronises the device). */
+void kdfmm_tree_destroy(kdfmm_tree t);
+
+/* kd-tree construction and cell moments (Sec. 2; Eq. 7).
+ * x: N x 3 positions, m: N masses (> 0), h: N smoothing lengths (> 0) for
+ * KDFMM_SOFT_M4 or NULL for Plummer softening.  The handle keeps its own
+ * tree-ordered copies; the caller's arrays may change after the call returns.
+ * Cells are cut through their centre of mass across the longest side of their
+ * bounding box (ties to the lowest axis); particles with x_axis < com_axis go
+ * left, stably; a cut that leaves one side empty splits by position.  Cells
+ * are numbered in pre-order.  The sums that decide a cut are pairwise
+ * (perfect binary tree over the cell's particles in ascending caller index,
+ * zero-padded to a power of two), so the tree is reproducible bit for bit.
+ * Synchronises `stream` (the host sizes later launches from device counters).
+ * Errors: KDFMM_ERR_INVALID_ARG for n < 1, bad params or NULL pointers,
+ * KDFMM_ERR_NONFINITE for NaN/Inf inputs or m <= 0 / h <= 0. */
+int kdfmm_tree_build(kdfmm_tree t, const double* x, const double* m, const double* h, int64_t n,
+                     const kdfmm_params* p, void* stream);
+
+/* Recomputes the cell moments (M, centre of mass, s, h_max, Q) of the existing
+ * topology for new positions/masses/smoothing lengths of the same particles
+ * (same caller order, same n).  Used to evaluate the force with the tree frozen.
+ * Sums run in pairwise order over each cell's particles in tree order. */
+int kdfmm_tree_moments(kdfmm_tree t, const double* x, const double* m, const double* h,
+                       void* stream);
+
+/* One force evaluation on the built tree: leaf-only walk with Eqs. 4-5,
+ * M2L (Eq. 6), L2P (Eq. 8), softened P2P (Eq. 13 / Plummer), a = a_short +
+ * a_long (Eq. 3).  a: N x 3 output, phi: N output potential or NULL (the
+ * potential is the third-order expansion of -M/R - Q_jk R_j R_k/(2R^5) plus
+ * the softened pair potentials).  Synchronises `stream` once (list sizes). */
+int kdfmm_fmm_accel(kdfmm_tree t, double* a, double* phi, void* stream);
+
+/* Vector-Jacobian product of the last evaluation's accelerations with respect
+ * to positions and masses, through the same tree and interaction lists (the
+ * lists and cell topology are held fixed).  a_bar: N x 3 cotangent; x_bar:
+ * N x 3 and m_bar: N outputs (overwritten).  The paper has no adjoint; this is
+ * the derivative of the evaluation that kdfmm_fmm_accel performs. */
+int kdfmm_fmm_accel_vjp(kdfmm_tree t, const double* a_bar, double* x_bar, double* m_bar,
+                        void* stream);
+
+/* out[0..2] = sum_i m_i v_i (device pointer to 3 doubles), float64 with a
+ * compensated (two-sum) combination of per-block partials in a fixed order,
+ * so repeated calls give identical bits.  With v = accelerations this is the
+ * total force whose non-zero value the paper demonstrates (Sec. 4, Eq. 30). */
+int kdfmm_total_momentum(const double* m, const double* v, int64_t n, double* out, void* stream);
+
+/* Host copies of the handle's statistics (KDFMM_NSTATS int64, host). */
+int kdfmm_tree_stats(kdfmm_tree t, int64_t* stats);
+
+/* Copies the tree and the last evaluation's interaction lists to HOST arrays
+ * sized from kdfmm_tree_stats: perm (N int64: tree position -> caller index);
+ * cell_ints (ncells x 7 int64: first, count, left, right, parent, depth, skip);
+ * cell_reals (ncells x 12 double: M, com x y z, s, h_max, Q xx xy xz yy yz zz);
+ * leaf_ids (nleaves int32, ascending); far_off / near_off (nleaves + 1 int64);
+ * far_idx (NFAR int32) and near_idx (NNEAR int32), ascending within each leaf.
+ * Any pointer may be NULL to skip that array.  Synchronises the device. */
+int kdfmm_tree_export(kdfmm_tree t, int64_t* perm, int64_t* cell_ints, double* cell_reals,
+                      int32_t* leaf_ids, int64_t* far_off, int32_t* far_idx, int64_t* near_off,
+                      int32_t* near_idx);
+
+/* Tracing (no counterpart in the paper): with enable = 1 the handle records
+ * CUDA events on the caller's stream around each phase of kdfmm_tree_build and
+ * kdfmm_fmm_accel.  ms (host, KDFMM_NPHASES floats, may be NULL) receives the
+ * durations of the most recent timed call of each phase; the call waits for
+ * those events.  enable = 0 stops recording.  Timing changes no result. */
+int kdfmm_tree_timing(kdfmm_tree t, int enable, float* ms);
+
+/* Message for the calling thread's most recent failure ("" if none). */
+const char* kdfmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KDFMM_H */

@@ -1,0 +1,307 @@
+// C ABI of the kdfmm library (declared in include/kdfmm.h): argument
+// checking, device buffers owned by the handle, and the order of the steps of
+// one force evaluation.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "kdfmm_internal.cuh"
+
+namespace kdfmm {
+
+void free_build_buffers(kdfmm_tree_s* t);
+int64_t momentum_blocks(int64_t n);
+
+namespace {
+thread_local char g_err[512] = "";
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+int check_params(const kdfmm_params* p, const double* h) {
+  if (!p) return set_error(KDFMM_ERR_INVALID_ARG, "params is NULL");
+  if (!(p->theta >= 0.0 && p->theta <= 1.0))
+    return set_error(KDFMM_ERR_INVALID_ARG, "theta must lie in [0, 1] (got %g)", p->theta);
+  if (p->n_leaf < 1 || p->n_leaf > KDFMM_MAX_LEAF)
+    return set_error(KDFMM_ERR_INVALID_ARG, "n_leaf must lie in [1, %d] (got %d)", KDFMM_MAX_LEAF,
+                     p->n_leaf);
+  if (p->soft_kind != KDFMM_SOFT_PLUMMER && p->soft_kind != KDFMM_SOFT_M4)
+    return set_error(KDFMM_ERR_INVALID_ARG, "unknown soft_kind %d", p->soft_kind);
+  if (p->precision != KDFMM_FP64 && p->precision != KDFMM_MIXED)
+    return set_error(KDFMM_ERR_INVALID_ARG, "unknown precision %d", p->precision);
+  if (!(std::isfinite(p->eps) && p->eps >= 0.0))
+    return set_error(KDFMM_ERR_INVALID_ARG, "eps must be finite and >= 0");
+  if (!(std::isfinite(p->r_kern) && p->r_kern >= 0.0))
+    return set_error(KDFMM_ERR_INVALID_ARG, "r_kern must be finite and >= 0");
+  if (p->reserved != 0) return set_error(KDFMM_ERR_INVALID_ARG, "reserved must be 0");
+  if (p->soft_kind == KDFMM_SOFT_M4 && h == nullptr)
+    return set_error(KDFMM_ERR_INVALID_ARG, "M4 kernel softening needs smoothing lengths h");
+  return KDFMM_OK;
+}
+
+}  // namespace
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int check_cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return KDFMM_OK;
+  return set_error(KDFMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void phase_begin(kdfmm_tree_s* t, int phase, cudaStream_t s) {
+  if (!t->timing) return;
+  if (!t->ev[2 * phase]) {
+    cudaEventCreate(&t->ev[2 * phase]);
+    cudaEventCreate(&t->ev[2 * phase + 1]);
+  }
+  cudaEventRecord(t->ev[2 * phase], s);
+}
+
+void phase_end(kdfmm_tree_s* t, int phase, cudaStream_t s) {
+  if (!t->timing || !t->ev[2 * phase + 1]) return;
+  cudaEventRecord(t->ev[2 * phase + 1], s);
+  t->ev_used[phase] = true;
+}
+
+static int grow_eval_buffers(kdfmm_tree_s* t, int64_t cap) {
+  Lists& L = t->L;
+  cudaFree(L.far_cnt); cudaFree(L.near_cnt); cudaFree(L.far_off); cudaFree(L.near_off);
+  L.far_cnt = L.near_cnt = nullptr;
+  L.far_off = L.near_off = nullptr;
+  if (cudaMalloc(&L.far_cnt, (cap + 1) * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&L.near_cnt, (cap + 1) * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&L.far_off, (cap + 2) * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&L.near_off, (cap + 2) * sizeof(int64_t)) != cudaSuccess)
+    return set_error(KDFMM_ERR_OOM, "interaction list offsets");
+  return KDFMM_OK;
+}
+
+}  // namespace kdfmm
+
+using namespace kdfmm;
+
+extern "C" {
+
+const char* kdfmm_last_error(void) { return g_err; }
+
+int kdfmm_tree_create(kdfmm_tree* out) {
+  if (!out) return set_error(KDFMM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  kdfmm_tree_s* t = new (std::nothrow) kdfmm_tree_s();
+  if (!t) return set_error(KDFMM_ERR_OOM, "handle allocation");
+  int rc = check_cuda(cudaGetDevice(&t->device), "cudaGetDevice");
+  if (!rc) rc = check_cuda(cudaMalloc(&t->counters, 32 * sizeof(int32_t)), "counters");
+  if (!rc) rc = check_cuda(cudaMalloc(&t->status, sizeof(int32_t)), "status");
+  if (!rc) rc = check_cuda(cudaMalloc(&t->com_bound, sizeof(float)), "bound");
+  if (!rc) rc = check_cuda(cudaMalloc(&t->L.near_np, 4 * sizeof(int64_t)), "stats");
+  if (!rc) rc = check_cuda(cudaHostAlloc(&t->host_stats, 64 * sizeof(int64_t), 0), "host stats");
+  if (!rc) rc = check_cuda(cudaHostAlloc(&t->host_counters, 64 * sizeof(int32_t), 0), "host counters");
+  if (rc) {
+    kdfmm_tree_destroy(t);
+    return rc;
+  }
+  memset(t->host_stats, 0, 64 * sizeof(int64_t));
+  *out = t;
+  return KDFMM_OK;
+}
+
+void kdfmm_tree_destroy(kdfmm_tree t) {
+  if (!t) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaSetDevice(t->device);
+  cudaDeviceSynchronize();
+  free_build_buffers(t);
+  cudaFree(t->counters); cudaFree(t->status); cudaFree(t->com_bound);
+  cudaFree(t->L.far_cnt); cudaFree(t->L.near_cnt); cudaFree(t->L.far_off); cudaFree(t->L.near_off);
+  cudaFree(t->L.far_idx); cudaFree(t->L.near_idx); cudaFree(t->L.near_np);
+  cudaFree(t->mom_partial);
+  for (cudaEvent_t& e : t->ev)
+    if (e) cudaEventDestroy(e);
+  if (t->host_stats) cudaFreeHost(t->host_stats);
+  if (t->host_counters) cudaFreeHost(t->host_counters);
+  cudaGetLastError();
+  cudaSetDevice(dev);
+  delete t;
+}
+
+int kdfmm_tree_build(kdfmm_tree t, const double* x, const double* m, const double* h, int64_t n,
+                     const kdfmm_params* p, void* stream) {
+  if (!t) return set_error(KDFMM_ERR_INVALID_ARG, "tree is NULL");
+  int rc = check_params(p, h);
+  if (rc) return rc;
+  if (n < 1 || n > (int64_t(1) << 30))
+    return set_error(KDFMM_ERR_INVALID_ARG, "n must lie in [1, 2^30] (got %lld)", (long long)n);
+  if (!is_device_ptr(x) || !is_device_ptr(m) || (h != nullptr && !is_device_ptr(h)))
+    return set_error(KDFMM_ERR_INVALID_ARG, "x, m (and h) must be device pointers");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return set_error(KDFMM_ERR_INVALID_ARG, "handle belongs to device %d", t->device);
+  t->built = t->evaluated = false;
+  t->n = n;
+  t->p = *p;
+  const int64_t old_cap = t->cap_n;
+  phase_begin(t, KDFMM_PHASE_BUILD, s);
+  if ((rc = build_tree(t, x, m, h, s))) return rc;
+  phase_end(t, KDFMM_PHASE_BUILD, s);
+  if (t->cap_n != old_cap || t->L.far_cnt == nullptr)
+    if ((rc = grow_eval_buffers(t, t->cap_n))) return rc;
+  t->built = true;
+  int64_t* hs = t->host_stats;
+  hs[KDFMM_STAT_N] = n;
+  hs[KDFMM_STAT_NCELLS] = t->ncells;
+  hs[KDFMM_STAT_NLEAVES] = t->nleaves;
+  hs[KDFMM_STAT_DEPTH] = t->depth;
+  hs[KDFMM_STAT_NFAR] = hs[KDFMM_STAT_NNEAR] = hs[KDFMM_STAT_NP2P] = 0;
+  hs[KDFMM_STAT_NFALLBACK] = t->nfallback;
+  hs[KDFMM_STAT_NEXACT] = 0;
+  return KDFMM_OK;
+}
+
+int kdfmm_tree_moments(kdfmm_tree t, const double* x, const double* m, const double* h,
+                       void* stream) {
+  if (!t || !t->built) return set_error(KDFMM_ERR_INVALID_ARG, "tree not built");
+  if (!is_device_ptr(x) || !is_device_ptr(m) || (h != nullptr && !is_device_ptr(h)))
+    return set_error(KDFMM_ERR_INVALID_ARG, "x, m (and h) must be device pointers");
+  if (t->p.soft_kind == KDFMM_SOFT_M4 && h == nullptr)
+    return set_error(KDFMM_ERR_INVALID_ARG, "M4 kernel softening needs smoothing lengths h");
+  t->evaluated = false;
+  return recompute_moments(t, x, m, h, static_cast<cudaStream_t>(stream));
+}
+
+int kdfmm_fmm_accel(kdfmm_tree t, double* a, double* phi, void* stream) {
+  if (!t || !t->built) return set_error(KDFMM_ERR_INVALID_ARG, "tree not built");
+  if (!is_device_ptr(a) || (phi != nullptr && !is_device_ptr(phi)))
+    return set_error(KDFMM_ERR_INVALID_ARG, "a (and phi) must be device pointers");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  phase_begin(t, KDFMM_PHASE_WALK, s);
+  int rc = run_walk(t, s);
+  if (rc) return rc;
+  phase_end(t, KDFMM_PHASE_WALK, s);
+  phase_begin(t, KDFMM_PHASE_M2L, s);
+  if ((rc = run_m2l(t, s))) return rc;
+  phase_end(t, KDFMM_PHASE_M2L, s);
+  phase_begin(t, KDFMM_PHASE_P2P, s);
+  if ((rc = run_p2p(t, a, phi, s))) return rc;
+  phase_end(t, KDFMM_PHASE_P2P, s);
+  t->evaluated = true;
+  return KDFMM_OK;
+}
+
+int kdfmm_total_momentum(const double* m, const double* v, int64_t n, double* out, void* stream) {
+  if (n < 1) return set_error(KDFMM_ERR_INVALID_ARG, "n must be >= 1");
+  if (!is_device_ptr(m) || !is_device_ptr(v) || !is_device_ptr(out))
+    return set_error(KDFMM_ERR_INVALID_ARG, "m, v and out must be device pointers");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t nb = momentum_blocks(n);
+  double* scratch = nullptr;
+  int rc = check_cuda(cudaMallocAsync(&scratch, (size_t)nb * 6 * sizeof(double), s), "momentum scratch");
+  if (rc) return rc;
+  rc = momentum(m, v, n, out, scratch, s);
+  cudaFreeAsync(scratch, s);
+  return rc;
+}
+
+int kdfmm_tree_stats(kdfmm_tree t, int64_t* stats) {
+  if (!t || !stats) return set_error(KDFMM_ERR_INVALID_ARG, "NULL argument");
+  int64_t* hs = t->host_stats;
+  if (t->evaluated) {
+    int64_t dev[2] = {0, 0};
+    int rc = check_cuda(cudaMemcpy(dev, t->L.near_np, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost),
+                        "stats copy");
+    if (rc) return rc;
+    hs[KDFMM_STAT_NP2P] = dev[0];
+    hs[KDFMM_STAT_NEXACT] = dev[1];
+  }
+  hs[KDFMM_STAT_LAUNCHES] = t->launches;
+  memcpy(stats, hs, KDFMM_NSTATS * sizeof(int64_t));
+  return KDFMM_OK;
+}
+
+int kdfmm_tree_timing(kdfmm_tree t, int enable, float* ms) {
+  if (!t) return set_error(KDFMM_ERR_INVALID_ARG, "tree is NULL");
+  if (ms) {
+    for (int k = 0; k < KDFMM_NPHASES; ++k) {
+      ms[k] = 0.0f;
+      if (!t->ev_used[k]) continue;
+      int rc = check_cuda(cudaEventSynchronize(t->ev[2 * k + 1]), "timing sync");
+      if (rc) return rc;
+      rc = check_cuda(cudaEventElapsedTime(&ms[k], t->ev[2 * k], t->ev[2 * k + 1]), "elapsed");
+      if (rc) return rc;
+    }
+  }
+  t->timing = enable != 0;
+  return KDFMM_OK;
+}
+
+int kdfmm_tree_export(kdfmm_tree t, int64_t* perm, int64_t* cell_ints, double* cell_reals,
+                      int32_t* leaf_ids, int64_t* far_off, int32_t* far_idx, int64_t* near_off,
+                      int32_t* near_idx) {
+  if (!t || !t->built) return set_error(KDFMM_ERR_INVALID_ARG, "tree not built");
+  int rc = check_cuda(cudaDeviceSynchronize(), "export sync");
+  if (rc) return rc;
+  const int64_t n = t->n, nc = t->ncells, nl = t->nleaves;
+  auto D2H = [&](void* dst, const void* src, size_t bytes) {
+    return check_cuda(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost), "export copy");
+  };
+  if (perm) {
+    std::vector<int32_t> v(n);
+    if ((rc = D2H(v.data(), t->tp.idx, n * sizeof(int32_t)))) return rc;
+    for (int64_t i = 0; i < n; ++i) perm[i] = v[i];
+  }
+  if (cell_ints) {
+    const int32_t* cols[7] = {t->c.first, t->c.count, t->c.left, t->c.right,
+                              t->c.parent, t->c.depth, t->c.skip};
+    std::vector<int32_t> v(nc);
+    for (int k = 0; k < 7; ++k) {
+      if ((rc = D2H(v.data(), cols[k], nc * sizeof(int32_t)))) return rc;
+      for (int64_t c = 0; c < nc; ++c) cell_ints[7 * c + k] = v[c];
+    }
+  }
+  if (cell_reals) {
+    const double* cols[6] = {t->c.M, t->c.cx, t->c.cy, t->c.cz, t->c.s, t->c.hmax};
+    std::vector<double> v(6 * nc);
+    for (int k = 0; k < 6; ++k) {
+      if ((rc = D2H(v.data(), cols[k], nc * sizeof(double)))) return rc;
+      for (int64_t c = 0; c < nc; ++c) cell_reals[12 * c + k] = v[c];
+    }
+    if ((rc = D2H(v.data(), t->c.Q, 6 * nc * sizeof(double)))) return rc;
+    for (int64_t c = 0; c < nc; ++c)
+      for (int k = 0; k < 6; ++k) cell_reals[12 * c + 6 + k] = v[6 * c + k];
+  }
+  if (leaf_ids && (rc = D2H(leaf_ids, t->leaf_cells, nl * sizeof(int32_t)))) return rc;
+  if (far_off || far_idx || near_off || near_idx) {
+    if (!t->evaluated) return set_error(KDFMM_ERR_INVALID_ARG, "no evaluation to export lists from");
+    if (far_off && (rc = D2H(far_off, t->L.far_off, (nl + 1) * sizeof(int64_t)))) return rc;
+    if (near_off && (rc = D2H(near_off, t->L.near_off, (nl + 1) * sizeof(int64_t)))) return rc;
+    const int64_t nf = t->host_stats[KDFMM_STAT_NFAR], nn = t->host_stats[KDFMM_STAT_NNEAR];
+    if (far_idx && nf && (rc = D2H(far_idx, t->L.far_idx, nf * sizeof(int32_t)))) return rc;
+    if (near_idx && nn && (rc = D2H(near_idx, t->L.near_idx, nn * sizeof(int32_t)))) return rc;
+  }
+  return KDFMM_OK;
+}
+
+int kdfmm_fmm_accel_vjp(kdfmm_tree t, const double* a_bar, double* x_bar, double* m_bar,
+                        void* stream) {
+  (void)a_bar; (void)x_bar; (void)m_bar; (void)stream;
+  if (!t || !t->evaluated) return set_error(KDFMM_ERR_INVALID_ARG, "no evaluation to differentiate");
+  return set_error(KDFMM_ERR_INVALID_ARG, "adjoint not available in this build");
+}
+
+}  // extern "C"

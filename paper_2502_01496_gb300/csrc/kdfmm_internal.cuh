@@ -1,0 +1,290 @@
+// Internal declarations of the kdfmm CUDA library (sm_103a).  Not part of the
+// public ABI; include/kdfmm.h is.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kdfmm.h"
+
+namespace kdfmm {
+
+// ---------------------------------------------------------------------------
+// Tunables
+// ---------------------------------------------------------------------------
+constexpr int kChunk = 2048;           // phase-A reduction chunk (elements)
+constexpr int kChunkThreads = 256;     // 8 consecutive elements per thread
+constexpr int kSubtreeMax = 2048;      // cells this small finish in shared memory
+constexpr int kSubtreeThreads = 256;
+constexpr int kNumStatus = 4;
+
+// Device-side status bits (OR-ed into a device word, read after a sync).
+enum : int {
+  ST_NONFINITE = 1,
+  ST_CAPACITY = 2,
+  ST_INTERNAL = 4,
+  ST_TIMEOUT = 8,
+};
+
+// A contiguous run of tree positions that belongs to one cell during the build.
+struct Seg {
+  int32_t first;   // first tree position
+  int32_t count;   // particles
+  int32_t cell;    // build-order (temporary) cell id
+  int32_t dbuf;    // depth << 1 | buffer holding the particles
+};
+
+// Particle columns, float64, in one tree order.
+struct PCols {
+  double *x, *y, *z, *m, *h;
+  int32_t* idx;    // caller index
+};
+
+// Cells in build (temporary) order.
+struct TmpCells {
+  int32_t *first, *count, *left, *right, *depth;
+  double *M, *cx, *cy, *cz, *s;
+};
+
+// Cells in final pre-order.
+struct Cells {
+  int32_t *first, *count, *left, *right, *parent, *skip, *depth;
+  double *M, *cx, *cy, *cz, *s, *hmax;
+  double* Q;                 // 6 per cell: xx xy xz yy yz zz
+  // derived views
+  float4* walk;              // (com x y z, s) in float32 for the walk's filter
+  float2* walk2;             // (h_max, skip as int bits)
+  float4* src32;             // 4 per cell: (hi xyz, M), (lo xyz, 0), (Q xx xy xz yy), (Q yz zz, 0, 0)
+  double* src64;             // 10 per cell: com xyz, M, Q[6]
+  int32_t* ready;            // bottom-up arrival counters
+};
+
+struct Lists {
+  int32_t *far_cnt, *near_cnt;
+  int64_t *far_off, *near_off;     // nleaves + 1
+  int32_t *far_idx, *near_idx;
+  int64_t far_cap, near_cap;
+  int64_t* near_np;                // per leaf: sum of near-leaf sizes
+};
+
+}  // namespace kdfmm
+
+struct kdfmm_tree_s {
+  int device = 0;
+  int64_t n = 0, cap_n = 0;
+  int32_t ncells = 0, nleaves = 0, depth = 0, nfallback = 0;
+  int64_t cap_cells = 0;
+  kdfmm_params p{};
+  bool built = false, evaluated = false;
+
+  // build scratch
+  kdfmm::PCols buf[2]{};
+  kdfmm::Seg* segA[2]{};
+  kdfmm::Seg *segB = nullptr, *segL = nullptr;
+  int64_t capA = 0, capB = 0, capL = 0;
+  int32_t* counters = nullptr;     // device: [0] cells, [1] nextA, [2] nB, [3] nL, [4] chunks, [5] nfallback, [6] depth, [7] nexact
+  int32_t* status = nullptr;       // device status word
+  int32_t* chunk_seg = nullptr;
+  int32_t* seg_chunk_off = nullptr;
+  double* chunk_sum = nullptr;     // 4 per chunk
+  long long* chunk_key = nullptr;  // 6 per chunk: min xyz, max xyz
+  int32_t* chunk_left = nullptr;
+  int32_t* chunk_loff = nullptr;
+  long long* chunk_s2 = nullptr;
+  int32_t* seg_axis = nullptr;
+  double* seg_cut = nullptr;
+  int32_t* seg_nl = nullptr;
+  int64_t cap_chunks = 0, cap_segA = 0;
+  kdfmm::TmpCells tmp{};
+  int32_t *cnt_start = nullptr, *min_depth = nullptr, *start_off = nullptr;
+  int32_t* scan_tmp = nullptr;
+  int64_t cap_scan = 0;
+
+  // final tree
+  kdfmm::PCols tp{};               // tree order: x y z m h, idx = caller index
+  float4* pf = nullptr;            // (x - com_leaf, m) float32
+  float4* ph = nullptr;            // (1/h, 1/h^3, h, 0) float32
+  kdfmm::Cells c{};
+  int32_t* leaf_cells = nullptr;   // pre-order ids of the leaves
+  int32_t* leaf_rank = nullptr;    // cell -> leaf ordinal (-1 for super-cells)
+  float* com_bound = nullptr;      // device: max |com component| over cells
+  kdfmm::Lists L{};
+  double* lexp64 = nullptr;        // 20 per leaf
+  float* lexp32 = nullptr;         // 24 per leaf (20 coefficients + 4 low parts)
+
+  double* mom_partial = nullptr;   // total_momentum scratch
+  int64_t cap_mom = 0;
+  int64_t* host_stats = nullptr;   // pinned host mirror
+  int32_t* host_counters = nullptr;
+  int64_t launches = 0;            // kernels launched by this handle
+  bool timing = false;
+  cudaEvent_t ev[2 * KDFMM_NPHASES]{};
+  bool ev_used[KDFMM_NPHASES]{};
+};
+
+namespace kdfmm {
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+// Order-preserving int64 key of a double (for min / max with integer ops).
+__device__ __forceinline__ long long dkey(double v) {
+  long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dunkey(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
+struct Sum4 {
+  double m, x, y, z;
+};
+__device__ __forceinline__ Sum4 zero4() { return Sum4{0.0, 0.0, 0.0, 0.0}; }
+__device__ __forceinline__ Sum4 add4(const Sum4& a, const Sum4& b) {
+  return Sum4{__dadd_rn(a.m, b.m), __dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y), __dadd_rn(a.z, b.z)};
+}
+__device__ __forceinline__ Sum4 shfl_xor4(const Sum4& a, int o) {
+  return Sum4{__shfl_xor_sync(0xffffffffu, a.m, o), __shfl_xor_sync(0xffffffffu, a.x, o),
+              __shfl_xor_sync(0xffffffffu, a.y, o), __shfl_xor_sync(0xffffffffu, a.z, o)};
+}
+// Butterfly over the 32 lanes: lane l holds the sum of an aligned block l;
+// pairing (2j, 2j+1), then pairs of pairs... is the perfect binary tree, and
+// every lane ends with the full sum.
+__device__ __forceinline__ Sum4 warp_tree4(Sum4 v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) v = add4(v, shfl_xor4(v, o));
+  return v;
+}
+// The element (m, m x, m y, m z) of one particle, products correctly rounded.
+__device__ __forceinline__ Sum4 elem4(double m, double x, double y, double z) {
+  return Sum4{m, __dmul_rn(m, x), __dmul_rn(m, y), __dmul_rn(m, z)};
+}
+
+// Perfect binary tree over 2^LOGB consecutive elements starting at `base`,
+// entries at or beyond `count` reading as zero.
+template <int LOGB, class F>
+__device__ __forceinline__ Sum4 block_tree(int base, int count, const F& get) {
+  if constexpr (LOGB == 0) {
+    return base < count ? get(base) : zero4();
+  } else {
+    if (base >= count) return zero4();
+    constexpr int H = 1 << (LOGB - 1);
+    Sum4 l = block_tree<LOGB - 1>(base, count, get);
+    Sum4 r = block_tree<LOGB - 1>(base + H, count, get);
+    return add4(l, r);
+  }
+}
+
+// Canonical pairwise sum of `count` elements (count <= 2048) by one warp: the
+// sequence is padded to P = 2^ceil(log2 count); lane l sums its aligned block
+// of P/32 elements as a perfect tree, the butterfly combines the lanes.
+template <class F>
+__device__ __forceinline__ Sum4 warp_pairwise(int count, const F& get) {
+  const int lane = threadIdx.x & 31;
+  int P = 1;
+  while (P < count) P <<= 1;
+  Sum4 v;
+  if (P <= 32) {
+    v = lane < count ? get(lane) : zero4();
+  } else {
+    const int B = P >> 5;
+    const int base = lane * B;
+    switch (B) {
+      case 2: v = block_tree<1>(base, count, get); break;
+      case 4: v = block_tree<2>(base, count, get); break;
+      case 8: v = block_tree<3>(base, count, get); break;
+      case 16: v = block_tree<4>(base, count, get); break;
+      case 32: v = block_tree<5>(base, count, get); break;
+      default: v = block_tree<6>(base, count, get); break;
+    }
+  }
+  return warp_tree4(v);
+}
+
+__device__ __forceinline__ long long warp_min_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+__device__ __forceinline__ long long warp_max_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// Squared distance exactly as dx*dx + dy*dy + dz*dz (no contraction).
+__device__ __forceinline__ double dist2_rn(double x, double y, double z, double cx, double cy,
+                                           double cz) {
+  double dx = __dsub_rn(x, cx), dy = __dsub_rn(y, cy), dz = __dsub_rn(z, cz);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Longest side of a bounding box; ties go to the lowest axis.
+__device__ __forceinline__ int longest_axis(const double lo[3], const double hi[3]) {
+  double e0 = __dsub_rn(hi[0], lo[0]), e1 = __dsub_rn(hi[1], lo[1]), e2 = __dsub_rn(hi[2], lo[2]);
+  int axis = 0;
+  double best = e0;
+  if (e1 > best) { axis = 1; best = e1; }
+  if (e2 > best) { axis = 2; }
+  return axis;
+}
+
+// Error-free transformation a + b = s + e (Knuth two-sum), float32.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (hi, lo) += v with the rounding error of the high part carried in lo.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
+  float s, e;
+  two_sum(hi, v, s, e);
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+// (hi, lo) += (bh, bl)
+__device__ __forceinline__ void df_add2(float& hi, float& lo, float bh, float bl) {
+  float s, e;
+  two_sum(hi, bh, s, e);
+  hi = s;
+  lo = __fadd_rn(__fadd_rn(lo, bl), e);
+}
+__device__ __forceinline__ void two_sum_d(double a, double b, double& s, double& e) {
+  s = __dadd_rn(a, b);
+  double bb = __dsub_rn(s, a);
+  e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* h,
+               cudaStream_t s);
+int recompute_moments(kdfmm_tree_s* t, const double* x, const double* m, const double* h,
+                      cudaStream_t s);
+int run_walk(kdfmm_tree_s* t, cudaStream_t s);
+int run_m2l(kdfmm_tree_s* t, cudaStream_t s);
+int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s);
+int momentum(const double* m, const double* v, int64_t n, double* out, double* scratch,
+             cudaStream_t s);
+// exclusive scan of n int32 (out may alias in); returns the total in *total_dev
+void scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, cudaStream_t s);
+void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s);
+int64_t scan_tmp_elems(int64_t n);
+
+// tracing (api.cu): CUDA events around a phase when timing is enabled
+void phase_begin(kdfmm_tree_s* t, int phase, cudaStream_t s);
+void phase_end(kdfmm_tree_s* t, int phase, cudaStream_t s);
+
+// error plumbing (api.cu)
+int set_error(int code, const char* fmt, ...);
+int check_cuda(cudaError_t e, const char* what);
+
+}  // namespace kdfmm

@@ -1,0 +1,216 @@
+// M2L (Sec. 2, Eq. 6): the field of a source cell beta (mass M, traceless
+// quadrupole Q of Eq. 7) about the sink leaf's centre of mass, r = com_alpha -
+// com_beta, expanded so that L2P (Eq. 8) can evaluate it at the particles.
+//
+// The local expansion is stored as the Cartesian derivatives of the potential
+//   Phi(R) = -M/R - Q_jk R_j R_k / (2 R^5) = -M D0 - (1/6) Q_jk D2_jk,
+// D_n = grad^n (1/R), up to third order (20 numbers): C0 = Phi, C1 = grad Phi,
+// C2, C3.  Eq. 6 is a = -C1 and the Taylor terms of Eq. 8 are -C2 x and
+// -(1/2) C3 x x.  With g_n the n-th derivative of (2 rho)^(-1/2) at rho =
+// R^2/2 (g_n = (-1)^n (2n-1)!! / R^(2n+1)), q = R.Q.R and u = Q.R:
+//   C0    = -M g0 - g2 q / 6
+//   C1_i  = s1 R_i + t2 u_i
+//   C2_ab = s2 R_a R_b + s1 d_ab + t3 (R_a u_b + R_b u_a) + t2 Q_ab
+//   C3_abc= s3 R_a R_b R_c + s2 (d_ab R_c + d_ac R_b + d_bc R_a)
+//         + t4 (R_b R_c u_a + R_a R_c u_b + R_a R_b u_c)
+//         + t3 (R_a Q_bc + R_b Q_ac + R_c Q_ab + d_ab u_c + d_ac u_b + d_bc u_a)
+// with s_n = -M g_n - g_(n+2) q / 6 and t_n = -g_n / 3.
+//
+// One warp per sink leaf; its lanes take the far cells in turn.  Mixed mode
+// works in float32 with the centre-of-mass difference formed from
+// (high, low) float pairs and compensated sums for C0 and C1; FP64 mode works
+// in float64 throughout.
+#include "kdfmm_internal.cuh"
+
+namespace kdfmm {
+
+namespace {
+
+template <class T>
+__device__ __forceinline__ T rsqrt_t(T v);
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double v) { return 1.0 / sqrt(v); }
+
+template <class T>
+__device__ __forceinline__ T c2e(int a, int b, const T R[3], const T u[3], const T Qm[3][3], T s1,
+                                 T s2, T t2, T t3) {
+  T v = s2 * R[a] * R[b] + t3 * (R[a] * u[b] + R[b] * u[a]) + t2 * Qm[a][b];
+  if (a == b) v += s1;
+  return v;
+}
+
+template <class T>
+__device__ __forceinline__ T c3e(int a, int b, int c, const T R[3], const T u[3], const T Qm[3][3],
+                                 T s2, T s3, T t3, T t4) {
+  T d = (a == b ? R[c] : T(0)) + (a == c ? R[b] : T(0)) + (b == c ? R[a] : T(0));
+  T du = (a == b ? u[c] : T(0)) + (a == c ? u[b] : T(0)) + (b == c ? u[a] : T(0));
+  return s3 * R[a] * R[b] * R[c] + s2 * d +
+         t4 * (R[b] * R[c] * u[a] + R[a] * R[c] * u[b] + R[a] * R[b] * u[c]) +
+         t3 * (R[a] * Qm[b][c] + R[b] * Qm[a][c] + R[c] * Qm[a][b] + du);
+}
+
+// Local coefficients of one source: out[0] C0; [1..3] C1 x y z; [4..9] C2 xx
+// xy xz yy yz zz; [10..19] C3 xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz.
+template <class T>
+__device__ __forceinline__ void m2l_coeffs(T Rx, T Ry, T Rz, T M, const T Q[6], T out[20]) {
+  const T R[3] = {Rx, Ry, Rz};
+  const T Qm[3][3] = {{Q[0], Q[1], Q[2]}, {Q[1], Q[3], Q[4]}, {Q[2], Q[4], Q[5]}};
+  const T R2 = Rx * Rx + Ry * Ry + Rz * Rz;
+  const T g0 = rsqrt_t<T>(R2);
+  const T i2 = g0 * g0;
+  const T g1 = -g0 * i2;
+  const T g2 = T(-3) * g1 * i2;
+  const T g3 = T(-5) * g2 * i2;
+  const T g4 = T(-7) * g3 * i2;
+  const T g5 = T(-9) * g4 * i2;
+  T u[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) u[i] = Qm[i][0] * Rx + Qm[i][1] * Ry + Qm[i][2] * Rz;
+  const T q = Rx * u[0] + Ry * u[1] + Rz * u[2];
+  const T sixth = T(1) / T(6), third = T(1) / T(3);
+  const T qs = q * sixth;
+  const T s1 = -M * g1 - g3 * qs;
+  const T s2 = -M * g2 - g4 * qs;
+  const T s3 = -M * g3 - g5 * qs;
+  const T t2 = -g2 * third, t3 = -g3 * third, t4 = -g4 * third;
+  out[0] = -M * g0 - g2 * qs;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) out[1 + i] = s1 * R[i] + t2 * u[i];
+  out[4] = c2e<T>(0, 0, R, u, Qm, s1, s2, t2, t3);
+  out[5] = c2e<T>(0, 1, R, u, Qm, s1, s2, t2, t3);
+  out[6] = c2e<T>(0, 2, R, u, Qm, s1, s2, t2, t3);
+  out[7] = c2e<T>(1, 1, R, u, Qm, s1, s2, t2, t3);
+  out[8] = c2e<T>(1, 2, R, u, Qm, s1, s2, t2, t3);
+  out[9] = c2e<T>(2, 2, R, u, Qm, s1, s2, t2, t3);
+  out[10] = c3e<T>(0, 0, 0, R, u, Qm, s2, s3, t3, t4);
+  out[11] = c3e<T>(0, 0, 1, R, u, Qm, s2, s3, t3, t4);
+  out[12] = c3e<T>(0, 0, 2, R, u, Qm, s2, s3, t3, t4);
+  out[13] = c3e<T>(0, 1, 1, R, u, Qm, s2, s3, t3, t4);
+  out[14] = c3e<T>(0, 1, 2, R, u, Qm, s2, s3, t3, t4);
+  out[15] = c3e<T>(0, 2, 2, R, u, Qm, s2, s3, t3, t4);
+  out[16] = c3e<T>(1, 1, 1, R, u, Qm, s2, s3, t3, t4);
+  out[17] = c3e<T>(1, 1, 2, R, u, Qm, s2, s3, t3, t4);
+  out[18] = c3e<T>(1, 2, 2, R, u, Qm, s2, s3, t3, t4);
+  out[19] = c3e<T>(2, 2, 2, R, u, Qm, s2, s3, t3, t4);
+}
+
+struct M2LArgs {
+  const int32_t* leaf_cells;
+  int nleaves;
+  const int64_t* far_off;
+  const int32_t* far_idx;
+  const float4* src32;
+  const double* src64;
+  float* lexp32;
+  double* lexp64;
+};
+
+__global__ void __launch_bounds__(256) k_m2l_mixed(M2LArgs A) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= A.nleaves) return;
+  const int a = A.leaf_cells[k];
+  const float4 ah = A.src32[4 * a], al = A.src32[4 * a + 1];
+  float acc[20], lo[4];
+#pragma unroll
+  for (int j = 0; j < 20; ++j) acc[j] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) lo[j] = 0.0f;
+  const int64_t off = A.far_off[k], nf = A.far_off[k + 1] - off;
+  for (int64_t e = lane; e < nf; e += 32) {
+    const int b = A.far_idx[off + e];
+    const float4 b0 = A.src32[4 * b], b1 = A.src32[4 * b + 1], b2 = A.src32[4 * b + 2],
+                 b3 = A.src32[4 * b + 3];
+    const float Rx = (ah.x - b0.x) + (al.x - b1.x);
+    const float Ry = (ah.y - b0.y) + (al.y - b1.y);
+    const float Rz = (ah.z - b0.z) + (al.z - b1.z);
+    const float Q[6] = {b2.x, b2.y, b2.z, b2.w, b3.x, b3.y};
+    float C[20];
+    m2l_coeffs<float>(Rx, Ry, Rz, b0.w, Q, C);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) df_add(acc[j], lo[j], C[j]);
+#pragma unroll
+    for (int j = 4; j < 20; ++j) acc[j] += C[j];
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float bh = __shfl_xor_sync(0xffffffffu, acc[j], o);
+      float bl = __shfl_xor_sync(0xffffffffu, lo[j], o);
+      df_add2(acc[j], lo[j], bh, bl);
+    }
+#pragma unroll
+    for (int j = 4; j < 20; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+  }
+  float* out = A.lexp32 + 24 * (int64_t)k;
+  if (lane < 20) {
+    float v = acc[0];
+#pragma unroll
+    for (int j = 1; j < 20; ++j) v = lane == j ? acc[j] : v;
+    out[lane] = v;
+  } else if (lane < 24) {
+    float v = lo[0];
+#pragma unroll
+    for (int j = 1; j < 4; ++j) v = lane - 20 == j ? lo[j] : v;
+    out[lane] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_m2l_fp64(M2LArgs A) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= A.nleaves) return;
+  const int a = A.leaf_cells[k];
+  const double* sa = A.src64 + 10 * (int64_t)a;
+  const double ax = sa[0], ay = sa[1], az = sa[2];
+  double acc[20];
+#pragma unroll
+  for (int j = 0; j < 20; ++j) acc[j] = 0.0;
+  const int64_t off = A.far_off[k], nf = A.far_off[k + 1] - off;
+  for (int64_t e = lane; e < nf; e += 32) {
+    const int b = A.far_idx[off + e];
+    const double* sb = A.src64 + 10 * (int64_t)b;
+    double C[20];
+    m2l_coeffs<double>(ax - sb[0], ay - sb[1], az - sb[2], sb[3], sb + 4, C);
+#pragma unroll
+    for (int j = 0; j < 20; ++j) acc[j] += C[j];
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int j = 0; j < 20; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+  }
+  double* out = A.lexp64 + 20 * (int64_t)k;
+  if (lane < 20) {
+    double v = acc[0];
+#pragma unroll
+    for (int j = 1; j < 20; ++j) v = lane == j ? acc[j] : v;
+    out[lane] = v;
+  }
+}
+
+inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+int run_m2l(kdfmm_tree_s* t, cudaStream_t s) {
+  M2LArgs A{};
+  A.leaf_cells = t->leaf_cells;
+  A.nleaves = t->nleaves;
+  A.far_off = t->L.far_off;
+  A.far_idx = t->L.far_idx;
+  A.src32 = t->c.src32;
+  A.src64 = t->c.src64;
+  A.lexp32 = t->lexp32;
+  A.lexp64 = t->lexp64;
+  const unsigned g = blocks_for((int64_t)t->nleaves * 32, 256);
+  if (t->p.precision == KDFMM_MIXED) k_m2l_mixed<<<g, 256, 0, s>>>(A);
+  else k_m2l_fp64<<<g, 256, 0, s>>>(A);
+  t->launches += 1;
+  return check_cuda(cudaGetLastError(), "m2l launch");
+}
+
+}  // namespace kdfmm

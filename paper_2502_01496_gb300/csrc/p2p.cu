@@ -1,0 +1,318 @@
+// Short-range direct summation (P2P) over each leaf's near list, L2P (Eq. 8)
+// of its local expansion, and the assembly a = a_short + a_long (Eq. 3) in
+// the caller's particle order.
+//
+// Pair interaction on particle i from j (d = x_i - x_j, j != i):
+//   Plummer:   a = -m_j d / (d^2 + eps^2)^(3/2),  phi = -m_j / sqrt(d^2 + eps^2);
+//   M4 kernel: the symmetrised Green's function of Eq. 13,
+//              a = -m_j [g(r,h_i) + g(r,h_j)]/2 d/r,  phi = -m_j [psi(r,h_i) + psi(r,h_j)]/2,
+//              with g = F(q)/r^2 (F the mass fraction of the cubic spline inside
+//              q = r/h) and psi = P(q)/h; outside q = 2 they are 1/r^2 and 1/r
+//              (Eq. 15).  Written here as g/r = h^-3 F(q)/q^3.
+//
+// One warp per target leaf.  A leaf of n_t <= 32 targets uses K = 32 / n_t
+// source slices: lane = target + n_t * slice, slice k takes sources k, k+K, ...
+// of every near leaf, and the slices are combined at the end.
+//
+// Mixed mode: positions are float32 offsets from each particle's own leaf
+// centre of mass; the target is shifted by the difference of the two leaf
+// centres (from (high, low) float pairs), so no large coordinate enters the
+// float32 arithmetic.  Each near leaf's contribution is summed in float32 and
+// folded into a (high, low) accumulator with two-sum; the long-range part is
+// added in float64 at the end.  FP64 mode uses float64 absolute positions.
+#include "kdfmm_internal.cuh"
+
+namespace kdfmm {
+
+namespace {
+
+struct P2PArgs {
+  const int32_t* leaf_cells;
+  int nleaves;
+  const int32_t *cfirst, *ccount;
+  const int64_t* near_off;
+  const int32_t* near_idx;
+  const float4* src32;       // cell (hi, M), (lo, 0), ...
+  const float4* pf;          // (x - com_leaf, m)
+  const float4* ph;          // (1/h, 1/h^3, h, 0)
+  PCols tp;                  // float64 tree-order particles
+  const double* cx;
+  const double *cy, *cz;
+  const float* lexp32;
+  const double* lexp64;
+  float eps2f;
+  double eps2;
+  double* a;
+  double* phi;
+};
+
+// M4 cubic spline, q = r/h < 2: F(q)/q^3 and P(q) (qi = 1/q).
+__device__ __forceinline__ float m4_fq3(float q, float qi) {
+  if (q < 1.0f) return 1.3333333f + q * q * (-1.2f + 0.5f * q);
+  return 2.6666667f + q * (-3.0f + q * (1.2f - 0.16666667f * q)) - 0.06666667f * qi * qi * qi;
+}
+__device__ __forceinline__ float m4_pot(float q, float qi) {
+  const float q2 = q * q;
+  if (q < 1.0f) return 1.4f + q2 * (-0.6666667f + q2 * (0.3f - 0.1f * q));
+  return 1.6f + q2 * (-1.3333333f + q * (1.0f + q * (-0.3f + 0.033333335f * q))) - 0.06666667f * qi;
+}
+__device__ __forceinline__ double m4_fq3_d(double q, double qi) {
+  if (q < 1.0) return 4.0 / 3.0 + q * q * (-1.2 + 0.5 * q);
+  return 8.0 / 3.0 + q * (-3.0 + q * (1.2 - q / 6.0)) - qi * qi * qi / 15.0;
+}
+__device__ __forceinline__ double m4_pot_d(double q, double qi) {
+  const double q2 = q * q;
+  if (q < 1.0) return 1.4 + q2 * (-2.0 / 3.0 + q2 * (0.3 - 0.1 * q));
+  return 1.6 + q2 * (-4.0 / 3.0 + q * (1.0 + q * (-0.3 + q / 30.0))) - qi / 15.0;
+}
+
+// Interaction of one target with one source, float32, accumulated into f*.
+template <int SOFT>
+__device__ __forceinline__ void pair32(float rx, float ry, float rz, float mj, const float4& hi,
+                                       const float4& hj, float eps2, float& fx, float& fy,
+                                       float& fz, float& fp) {
+  if (SOFT == KDFMM_SOFT_PLUMMER) {
+    const float r2 = rx * rx + ry * ry + rz * rz + eps2;
+    const float inv = rsqrtf(r2);
+    const float minv = mj * inv;
+    const float f = minv * inv * inv;
+    fx -= f * rx; fy -= f * ry; fz -= f * rz;
+    fp -= minv;
+  } else {
+    const float r2 = fmaxf(rx * rx + ry * ry + rz * rz, 1e-30f);
+    const float inv = rsqrtf(r2);
+    const float r = r2 * inv;
+    const float qa = r * hi.x, qb = r * hj.x;
+    float f, p;
+    if (qa < 2.0f || qb < 2.0f) {
+      const float inv3 = inv * inv * inv;
+      const float fa = qa < 2.0f ? hi.y * m4_fq3(qa, inv * hi.z) : inv3;
+      const float fb = qb < 2.0f ? hj.y * m4_fq3(qb, inv * hj.z) : inv3;
+      const float pa = qa < 2.0f ? hi.x * m4_pot(qa, inv * hi.z) : inv;
+      const float pb = qb < 2.0f ? hj.x * m4_pot(qb, inv * hj.z) : inv;
+      f = 0.5f * (fa + fb);
+      p = 0.5f * (pa + pb);
+    } else {
+      f = inv * inv * inv;
+      p = inv;
+    }
+    const float mf = mj * f;
+    fx -= mf * rx; fy -= mf * ry; fz -= mf * rz;
+    fp -= mj * p;
+  }
+}
+
+template <int SOFT>
+__device__ __forceinline__ void pair64(double rx, double ry, double rz, double mj, double hi,
+                                       double hj, double eps2, double& fx, double& fy, double& fz,
+                                       double& fp) {
+  if (SOFT == KDFMM_SOFT_PLUMMER) {
+    const double r2 = rx * rx + ry * ry + rz * rz + eps2;
+    const double inv = 1.0 / sqrt(r2);
+    const double minv = mj * inv;
+    const double f = minv * inv * inv;
+    fx -= f * rx; fy -= f * ry; fz -= f * rz;
+    fp -= minv;
+  } else {
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    if (r2 == 0.0) {
+      fp -= mj * 0.5 * (1.4 / hi + 1.4 / hj);
+      return;
+    }
+    const double r = sqrt(r2);
+    const double inv = 1.0 / r;
+    const double qa = r / hi, qb = r / hj;
+    double f, p;
+    if (qa < 2.0 || qb < 2.0) {
+      const double inv3 = inv * inv * inv;
+      const double fa = qa < 2.0 ? m4_fq3_d(qa, hi * inv) / (hi * hi * hi) : inv3;
+      const double fb = qb < 2.0 ? m4_fq3_d(qb, hj * inv) / (hj * hj * hj) : inv3;
+      const double pa = qa < 2.0 ? m4_pot_d(qa, hi * inv) / hi : inv;
+      const double pb = qb < 2.0 ? m4_pot_d(qb, hj * inv) / hj : inv;
+      f = 0.5 * (fa + fb);
+      p = 0.5 * (pa + pb);
+    } else {
+      f = inv * inv * inv;
+      p = inv;
+    }
+    const double mf = mj * f;
+    fx -= mf * rx; fy -= mf * ry; fz -= mf * rz;
+    fp -= mj * p;
+  }
+}
+
+// L2P of the 20 coefficients at x: a = -(C1 + C2 x + C3 x x / 2),
+// phi = C0 + C1.x + x.C2.x/2 + C3 x x x / 6.  Returns the parts beyond the
+// leading C0 / C1 terms (which the caller adds in higher precision).
+template <class T>
+__device__ __forceinline__ void l2p_tail(const T* C, T x, T y, T z, T& ax, T& ay, T& az, T& p) {
+  const T v0 = C[4] * x + C[5] * y + C[6] * z;
+  const T v1 = C[5] * x + C[7] * y + C[8] * z;
+  const T v2 = C[6] * x + C[8] * y + C[9] * z;
+  const T xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+  const T w0 = C[10] * xx + C[13] * yy + C[15] * zz + T(2) * (C[11] * xy + C[12] * xz + C[14] * yz);
+  const T w1 = C[11] * xx + C[16] * yy + C[18] * zz + T(2) * (C[13] * xy + C[14] * xz + C[17] * yz);
+  const T w2 = C[12] * xx + C[17] * yy + C[19] * zz + T(2) * (C[14] * xy + C[15] * xz + C[18] * yz);
+  ax = -(v0 + T(0.5) * w0);
+  ay = -(v1 + T(0.5) * w1);
+  az = -(v2 + T(0.5) * w2);
+  p = (C[1] * x + C[2] * y + C[3] * z) + T(0.5) * (x * v0 + y * v1 + z * v2) +
+      (x * w0 + y * w1 + z * w2) / T(6);
+}
+
+template <int SOFT, bool SELF>
+__device__ __forceinline__ void near_leaf32(const P2PArgs& A, int fb, int nb, int sl, int K, int t,
+                                            float xs, float ys, float zs, const float4& hi,
+                                            float& fx, float& fy, float& fz, float& fp) {
+  for (int j = sl; j < nb; j += K) {
+    if (SELF && j == t) continue;
+    const float4 s = A.pf[fb + j];
+    float4 hj = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (SOFT == KDFMM_SOFT_M4) hj = A.ph[fb + j];
+    pair32<SOFT>(xs - s.x, ys - s.y, zs - s.z, s.w, hi, hj, A.eps2f, fx, fy, fz, fp);
+  }
+}
+
+template <int SOFT>
+__global__ void __launch_bounds__(256) k_p2p_mixed(P2PArgs A) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= A.nleaves) return;
+  const int a = A.leaf_cells[k];
+  const int fa = A.cfirst[a], nt = A.ccount[a];
+  const int K = 32 / nt;
+  const int t = lane % nt, sl = lane / nt;
+  const bool act = sl < K;
+  const float4 xa = A.pf[fa + t];
+  float4 hi = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (SOFT == KDFMM_SOFT_M4) hi = A.ph[fa + t];
+  const float4 ca = A.src32[4 * a], cal = A.src32[4 * a + 1];
+  float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, azh = 0.f, azl = 0.f, ph_ = 0.f, pl = 0.f;
+  const int64_t e0 = A.near_off[k], e1 = A.near_off[k + 1];
+  for (int64_t e = e0; e < e1; ++e) {
+    const int b = A.near_idx[e];
+    const int fb = A.cfirst[b], nb = A.ccount[b];
+    const float4 cb = A.src32[4 * b], cbl = A.src32[4 * b + 1];
+    // target relative to the source leaf's centre of mass
+    const float xs = xa.x - ((cb.x - ca.x) + (cbl.x - cal.x));
+    const float ys = xa.y - ((cb.y - ca.y) + (cbl.y - cal.y));
+    const float zs = xa.z - ((cb.z - ca.z) + (cbl.z - cal.z));
+    float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;
+    if (act) {
+      if (b == a) near_leaf32<SOFT, true>(A, fb, nb, sl, K, t, xs, ys, zs, hi, fx, fy, fz, fp);
+      else near_leaf32<SOFT, false>(A, fb, nb, sl, K, t, xs, ys, zs, hi, fx, fy, fz, fp);
+    }
+    df_add(axh, axl, fx);
+    df_add(ayh, ayl, fy);
+    df_add(azh, azl, fz);
+    df_add(ph_, pl, fp);
+  }
+  // combine the source slices of each target
+  for (int s = 1; s < K; ++s) {
+    const int src = t + s * nt;
+    const float bxh = __shfl_sync(0xffffffffu, axh, src), bxl = __shfl_sync(0xffffffffu, axl, src);
+    const float byh = __shfl_sync(0xffffffffu, ayh, src), byl = __shfl_sync(0xffffffffu, ayl, src);
+    const float bzh = __shfl_sync(0xffffffffu, azh, src), bzl = __shfl_sync(0xffffffffu, azl, src);
+    const float bph = __shfl_sync(0xffffffffu, ph_, src), bpl = __shfl_sync(0xffffffffu, pl, src);
+    if (sl == 0) {
+      df_add2(axh, axl, bxh, bxl);
+      df_add2(ayh, ayl, byh, byl);
+      df_add2(azh, azl, bzh, bzl);
+      df_add2(ph_, pl, bph, bpl);
+    }
+  }
+  if (sl != 0 || !act) return;
+  const float* C = A.lexp32 + 24 * (int64_t)k;
+  float tx, ty, tz, tp_;
+  l2p_tail<float>(C, xa.x, xa.y, xa.z, tx, ty, tz, tp_);
+  const double ax = (double)axh + (double)axl - ((double)C[1] + (double)C[21]) + (double)tx;
+  const double ay = (double)ayh + (double)ayl - ((double)C[2] + (double)C[22]) + (double)ty;
+  const double az = (double)azh + (double)azl - ((double)C[3] + (double)C[23]) + (double)tz;
+  const int64_t ci = A.tp.idx[fa + t];
+  A.a[3 * ci + 0] = ax;
+  A.a[3 * ci + 1] = ay;
+  A.a[3 * ci + 2] = az;
+  if (A.phi) A.phi[ci] = (double)ph_ + (double)pl + ((double)C[0] + (double)C[20]) + (double)tp_;
+}
+
+template <int SOFT>
+__global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= A.nleaves) return;
+  const int a = A.leaf_cells[k];
+  const int fa = A.cfirst[a], nt = A.ccount[a];
+  const int K = 32 / nt;
+  const int t = lane % nt, sl = lane / nt;
+  const bool act = sl < K;
+  const int64_t it = (int64_t)fa + t;
+  const double xi = A.tp.x[it], yi = A.tp.y[it], zi = A.tp.z[it], hi = A.tp.h[it];
+  double fx = 0.0, fy = 0.0, fz = 0.0, fp = 0.0;
+  const int64_t e0 = A.near_off[k], e1 = A.near_off[k + 1];
+  if (act) {
+    for (int64_t e = e0; e < e1; ++e) {
+      const int b = A.near_idx[e];
+      const int fb = A.cfirst[b], nb = A.ccount[b];
+      for (int j = sl; j < nb; j += K) {
+        if (b == a && j == t) continue;
+        const int64_t js = (int64_t)fb + j;
+        pair64<SOFT>(xi - A.tp.x[js], yi - A.tp.y[js], zi - A.tp.z[js], A.tp.m[js], hi, A.tp.h[js],
+                     A.eps2, fx, fy, fz, fp);
+      }
+    }
+  }
+  for (int s = 1; s < K; ++s) {
+    const int src = t + s * nt;
+    const double bx = __shfl_sync(0xffffffffu, fx, src), by = __shfl_sync(0xffffffffu, fy, src);
+    const double bz = __shfl_sync(0xffffffffu, fz, src), bp = __shfl_sync(0xffffffffu, fp, src);
+    if (sl == 0) { fx += bx; fy += by; fz += bz; fp += bp; }
+  }
+  if (sl != 0 || !act) return;
+  const double* C = A.lexp64 + 20 * (int64_t)k;
+  const double x = xi - A.cx[a], y = yi - A.cy[a], z = zi - A.cz[a];
+  double tx, ty, tz, tp_;
+  l2p_tail<double>(C, x, y, z, tx, ty, tz, tp_);
+  const int64_t ci = A.tp.idx[it];
+  A.a[3 * ci + 0] = fx + (tx - C[1]);
+  A.a[3 * ci + 1] = fy + (ty - C[2]);
+  A.a[3 * ci + 2] = fz + (tz - C[3]);
+  if (A.phi) A.phi[ci] = fp + (C[0] + tp_);
+}
+
+inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s) {
+  P2PArgs A{};
+  A.leaf_cells = t->leaf_cells;
+  A.nleaves = t->nleaves;
+  A.cfirst = t->c.first;
+  A.ccount = t->c.count;
+  A.near_off = t->L.near_off;
+  A.near_idx = t->L.near_idx;
+  A.src32 = t->c.src32;
+  A.pf = t->pf;
+  A.ph = t->ph;
+  A.tp = t->tp;
+  A.cx = t->c.cx; A.cy = t->c.cy; A.cz = t->c.cz;
+  A.lexp32 = t->lexp32;
+  A.lexp64 = t->lexp64;
+  A.eps2 = t->p.eps * t->p.eps;
+  A.eps2f = (float)A.eps2;
+  A.a = a;
+  A.phi = phi;
+  const unsigned g = blocks_for((int64_t)t->nleaves * 32, 256);
+  const bool m4 = t->p.soft_kind == KDFMM_SOFT_M4;
+  if (t->p.precision == KDFMM_MIXED) {
+    if (m4) k_p2p_mixed<KDFMM_SOFT_M4><<<g, 256, 0, s>>>(A);
+    else k_p2p_mixed<KDFMM_SOFT_PLUMMER><<<g, 256, 0, s>>>(A);
+  } else {
+    if (m4) k_p2p_fp64<KDFMM_SOFT_M4><<<g, 256, 0, s>>>(A);
+    else k_p2p_fp64<KDFMM_SOFT_PLUMMER><<<g, 256, 0, s>>>(A);
+  }
+  t->launches += 1;
+  return check_cuda(cudaGetLastError(), "p2p launch");
+}
+
+}  // namespace kdfmm
