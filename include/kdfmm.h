@@ -136,6 +136,23 @@ int kdfmm_fmm_accel_vjp(kdfmm_tree t, const double* a_bar, double* x_bar, double
  * total force whose non-zero value the paper demonstrates (Sec. 4, Eq. 30). */
 int kdfmm_total_momentum(const double* m, const double* v, int64_t n, double* out, void* stream);
 
+/* The same reduction as kdfmm_total_momentum, for callers that must not
+ * allocate device memory while they run: cudaMalloc and cudaFree can
+ * synchronise the whole device, can fail or stall when another allocator
+ * already holds the memory, and are off limits to code working inside a fixed
+ * memory budget.  The paper has no counterpart; it is an interface variant.
+ * This call allocates nothing: its scratch is a fixed 48 KiB array (1024
+ * partial sums of 6 doubles) that every GPU loading the library keeps until
+ * the process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) once; make that first call before any stream
+ * capture.  All calls share the array and each overwrites the partials it
+ * reads, so nothing needs clearing, but calls whose work overlaps on the GPU
+ * (e.g. on two streams at once) race on it.  n must lie in [1, 2^30];
+ * larger n, NULL or non-device pointers give KDFMM_ERR_INVALID_ARG.  Results
+ * are bit-identical to kdfmm_total_momentum's. */
+int kdfmm_total_momentum_noalloc(const double* m, const double* v, int64_t n, double* out,
+                                 void* stream);
+
 /* Host copies of the handle's statistics (KDFMM_NSTATS int64, host). */
 int kdfmm_tree_stats(kdfmm_tree t, int64_t* stats);
 

@@ -7,7 +7,8 @@ fallback.
 
 Functions carry the C names without the ``kdfmm_`` prefix:
 ``tree_create``, ``tree_destroy``, ``tree_build``, ``tree_moments``,
-``fmm_accel``, ``fmm_accel_vjp``, ``total_momentum``, ``tree_stats``,
+``fmm_accel``, ``fmm_accel_vjp``, ``total_momentum``, ``total_momentum_noalloc``,
+``tree_stats``, ``tree_timing``,
 ``tree_export``, ``last_error``.
 """
 from __future__ import annotations
@@ -71,6 +72,7 @@ def lib() -> ctypes.CDLL:
     L.kdfmm_fmm_accel.argtypes = [P, P, P, P]
     L.kdfmm_fmm_accel_vjp.argtypes = [P, P, P, P, P]
     L.kdfmm_total_momentum.argtypes = [P, P, i64, P, P]
+    L.kdfmm_total_momentum_noalloc.argtypes = [P, P, i64, P, P]
     L.kdfmm_tree_stats.argtypes = [P, P]
     L.kdfmm_tree_export.argtypes = [P, P, P, P, P, P, P, P, P]
     L.kdfmm_tree_timing.argtypes = [P, ctypes.c_int, P]
@@ -78,7 +80,8 @@ def lib() -> ctypes.CDLL:
     L.kdfmm_last_error.restype = ctypes.c_char_p
     L.kdfmm_last_error.argtypes = []
     for name in ("kdfmm_tree_create", "kdfmm_tree_build", "kdfmm_tree_moments", "kdfmm_fmm_accel",
-                 "kdfmm_fmm_accel_vjp", "kdfmm_total_momentum", "kdfmm_tree_stats",
+                 "kdfmm_fmm_accel_vjp", "kdfmm_total_momentum", "kdfmm_total_momentum_noalloc",
+                 "kdfmm_tree_stats",
                  "kdfmm_tree_export"):
         getattr(L, name).restype = i32
     _lib = L
@@ -163,6 +166,17 @@ def total_momentum(m, v, out, stream=None) -> None:
     _dev_f64(out, "out", (3,))
     _check(lib().kdfmm_total_momentum(_ptr(m), _ptr(v), n, _ptr(out), _stream(stream)),
            "total_momentum")
+
+
+def total_momentum_noalloc(m, v, out, stream=None) -> None:
+    """total_momentum without any device allocation (fixed library scratch);
+    see include/kdfmm.h for who needs it and its limits."""
+    n = m.shape[0]
+    _dev_f64(m, "m", (n,))
+    _dev_f64(v, "v", (n, 3))
+    _dev_f64(out, "out", (3,))
+    _check(lib().kdfmm_total_momentum_noalloc(_ptr(m), _ptr(v), n, _ptr(out), _stream(stream)),
+           "total_momentum_noalloc")
 
 
 def tree_stats(tree) -> dict:
