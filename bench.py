@@ -30,8 +30,8 @@ METRIC = "Mparticles/s per FMM force eval at θ=0.5: FP32-mixed vs FP64 GPU, sam
 UNIT = "Mparticles/s"
 # P2P floating-point work per particle-particle interaction (algorithmic count,
 # Newtonian part: 3 sub, r^2 with 2 FMA + 1 mul + 1 add, rsqrt, 3 mul, 3 FMA,
-# potential add; FMA = 2 flops)
-P2P_FLOPS_PER_INTERACTION = 20
+# potential add; FMA = 2 flops); the M4 kernel softening adds 10 per interaction
+P2P_FLOPS_PER_INTERACTION = {0: 20, 1: 30}
 # FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -320,12 +320,13 @@ def run_ours(args):
 
     # dominant kernel: P2P (+ L2P + assembly), one launch per step
     p2p_mean = statistics.mean(p2p_ms)
-    flops = st["np2p"] * P2P_FLOPS_PER_INTERACTION
+    flops = st["np2p"] * P2P_FLOPS_PER_INTERACTION[ps.soft_kind]
     achieved = flops / (p2p_mean / 1e3) / 1e12
     kernel_key = f"k_p2p_{args.precision}_{'m4' if ps.soft_kind == 1 else 'plummer'}"
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic_for(kernel_key),
                 "kernel": kernel_key, "flops_per_launch": flops,
+                "flops_per_interaction": P2P_FLOPS_PER_INTERACTION[ps.soft_kind],
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "launch_ms": p2p_mean}
     phase_mean = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}

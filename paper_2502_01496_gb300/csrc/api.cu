@@ -222,8 +222,8 @@ int kdfmm_tree_stats(kdfmm_tree t, int64_t* stats) {
   if (!t || !stats) return set_error(KDFMM_ERR_INVALID_ARG, "NULL argument");
   int64_t* hs = t->host_stats;
   if (t->evaluated) {
-    int64_t dev[2] = {0, 0};
-    int rc = check_cuda(cudaMemcpy(dev, t->L.near_np, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost),
+    int64_t dev[4] = {0, 0, 0, 0};
+    int rc = check_cuda(cudaMemcpy(dev, t->L.near_np, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost),
                         "stats copy");
     if (rc) return rc;
     hs[KDFMM_STAT_NP2P] = dev[0];
@@ -288,11 +288,29 @@ int kdfmm_tree_export(kdfmm_tree t, int64_t* perm, int64_t* cell_ints, double* c
   if (leaf_ids && (rc = D2H(leaf_ids, t->leaf_cells, nl * sizeof(int32_t)))) return rc;
   if (far_off || far_idx || near_off || near_idx) {
     if (!t->evaluated) return set_error(KDFMM_ERR_INVALID_ARG, "no evaluation to export lists from");
-    if (far_off && (rc = D2H(far_off, t->L.far_off, (nl + 1) * sizeof(int64_t)))) return rc;
-    if (near_off && (rc = D2H(near_off, t->L.near_off, (nl + 1) * sizeof(int64_t)))) return rc;
-    const int64_t nf = t->host_stats[KDFMM_STAT_NFAR], nn = t->host_stats[KDFMM_STAT_NNEAR];
-    if (far_idx && nf && (rc = D2H(far_idx, t->L.far_idx, nf * sizeof(int32_t)))) return rc;
-    if (near_idx && nn && (rc = D2H(near_idx, t->L.near_idx, nn * sizeof(int32_t)))) return rc;
+    std::vector<int32_t> fc(nl), nc(nl);
+    if ((rc = D2H(fc.data(), t->L.far_cnt, nl * sizeof(int32_t)))) return rc;
+    if ((rc = D2H(nc.data(), t->L.near_cnt, nl * sizeof(int32_t)))) return rc;
+    std::vector<int32_t> fs, ns;
+    if (far_idx) {
+      fs.resize((size_t)(nl * t->L.cap_far));
+      if ((rc = D2H(fs.data(), t->L.far_idx, fs.size() * sizeof(int32_t)))) return rc;
+    }
+    if (near_idx) {
+      ns.resize((size_t)(nl * t->L.cap_near));
+      if ((rc = D2H(ns.data(), t->L.near_idx, ns.size() * sizeof(int32_t)))) return rc;
+    }
+    int64_t fo = 0, no = 0;
+    for (int64_t k = 0; k < nl; ++k) {
+      if (far_off) far_off[k] = fo;
+      if (near_off) near_off[k] = no;
+      if (far_idx) memcpy(far_idx + fo, fs.data() + k * t->L.cap_far, fc[k] * sizeof(int32_t));
+      if (near_idx) memcpy(near_idx + no, ns.data() + k * t->L.cap_near, nc[k] * sizeof(int32_t));
+      fo += fc[k];
+      no += nc[k];
+    }
+    if (far_off) far_off[nl] = fo;
+    if (near_off) near_off[nl] = no;
   }
   return KDFMM_OK;
 }

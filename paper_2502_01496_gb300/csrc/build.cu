@@ -178,7 +178,8 @@ k_chunk_reduce(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_s
 // Warp per segment: pairwise tree over its chunk sums, centre of mass, axis, cut.
 __global__ void k_decide(const Seg* __restrict__ segs, int nA, const int32_t* __restrict__ seg_off,
                          const double* __restrict__ csum, const long long* __restrict__ ckey,
-                         TmpCells tmp, int32_t* __restrict__ seg_axis, double* __restrict__ seg_cut) {
+                         TmpCells tmp, int32_t* __restrict__ seg_axis, double* __restrict__ seg_cut,
+                         float* __restrict__ seg_xb, long long* __restrict__ seg_s2) {
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (s >= nA) return;
@@ -228,16 +229,21 @@ __global__ void k_decide(const Seg* __restrict__ segs, int nA, const int32_t* __
     tmp.M[c] = M; tmp.cx[c] = cx; tmp.cy[c] = cy; tmp.cz[c] = cz;
     seg_axis[s] = axis;
     seg_cut[s] = axis == 0 ? cx : (axis == 1 ? cy : cz);
+    double X = 0.0;
+    for (int d = 0; d < 3; ++d) X = fmax(X, fmax(fabs(dlo[d]), fabs(dhi[d])));
+    seg_xb[s] = (float)X * 1.000001f;
+    seg_s2[s] = 0;
   }
 }
 
-// Per chunk: particles left of the cut, and the exact max squared distance to
-// the centre of mass.
+// Per chunk: particles left of the cut, and the largest float32 estimate of
+// the squared distance to the centre of mass (coordinates truncated to
+// float32 with integer operations; the exact size follows in the scatter).
 __global__ void __launch_bounds__(kChunkThreads)
 k_chunk_count(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_seg,
               const int32_t* __restrict__ seg_off, const int32_t* __restrict__ counters, PCols p,
               TmpCells tmp, const int32_t* __restrict__ seg_axis, const double* __restrict__ seg_cut,
-              int32_t* __restrict__ cleft, long long* __restrict__ cs2) {
+              int32_t* __restrict__ cleft, float* __restrict__ cs2) {
   const int b = blockIdx.x;
   if (b >= counters[4]) return;
   const int s = chunk_seg[b];
@@ -246,33 +252,33 @@ k_chunk_count(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_se
   const int cnt = min(kChunk, g.count - rel0);
   const int64_t base = (int64_t)g.first + rel0;
   const int axis = seg_axis[s];
-  const double cut = seg_cut[s];
-  const double cx = tmp.cx[g.cell], cy = tmp.cy[g.cell], cz = tmp.cz[g.cell];
+  const long long ckey = dkey(seg_cut[s]);
+  const float cx = trunc_to_float(tmp.cx[g.cell]), cy = trunc_to_float(tmp.cy[g.cell]),
+              cz = trunc_to_float(tmp.cz[g.cell]);
   int nl = 0;
-  long long s2 = 0;
+  float s2 = 0.0f;
   for (int k = threadIdx.x; k < cnt; k += kChunkThreads) {
     int64_t i = base + k;
-    double px = p.x[i], py = p.y[i], pz = p.z[i];
-    double a = axis == 0 ? px : (axis == 1 ? py : pz);
-    nl += a < cut;
-    long long d2 = __double_as_longlong(dist2_rn(px, py, pz, cx, cy, cz));
-    s2 = max(s2, d2);
+    const double px = p.x[i], py = p.y[i], pz = p.z[i];
+    const double a = axis == 0 ? px : (axis == 1 ? py : pz);
+    nl += dkey(a) < ckey;
+    const float dx = trunc_to_float(px) - cx, dy = trunc_to_float(py) - cy, dz = trunc_to_float(pz) - cz;
+    s2 = fmaxf(s2, dx * dx + dy * dy + dz * dz);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     nl += __shfl_xor_sync(0xffffffffu, nl, o);
-    long long w2 = __shfl_xor_sync(0xffffffffu, s2, o);
-    s2 = max(s2, w2);
+    s2 = fmaxf(s2, __shfl_xor_sync(0xffffffffu, s2, o));
   }
   __shared__ int wn[kChunkThreads / 32];
-  __shared__ long long ws2[kChunkThreads / 32];
+  __shared__ float ws2[kChunkThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) { wn[w] = nl; ws2[w] = s2; }
   __syncthreads();
   if (threadIdx.x == 0) {
     int t = 0;
-    long long m2 = 0;
-    for (int q = 0; q < kChunkThreads / 32; ++q) { t += wn[q]; m2 = max(m2, ws2[q]); }
+    float m2 = 0.0f;
+    for (int q = 0; q < kChunkThreads / 32; ++q) { t += wn[q]; m2 = fmaxf(m2, ws2[q]); }
     cleft[b] = t;
     cs2[b] = m2;
   }
@@ -281,8 +287,9 @@ k_chunk_count(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_se
 // Warp per segment: offsets of the left particles per chunk, the split point,
 // s, and the two children.
 __global__ void k_split(const Seg* __restrict__ segs, int nA, const int32_t* __restrict__ seg_off,
-                        const int32_t* __restrict__ cleft, const long long* __restrict__ cs2,
-                        int32_t* __restrict__ cloff, int32_t* __restrict__ seg_nl, BuildArgs A,
+                        const int32_t* __restrict__ cleft, const float* __restrict__ cs2,
+                        int32_t* __restrict__ cloff, int32_t* __restrict__ seg_nl,
+                        const float* __restrict__ seg_xb, float* __restrict__ seg_thr2, BuildArgs A,
                         Seg* nextA, Seg* segB, Seg* segL, int dst_buf) {
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -291,11 +298,11 @@ __global__ void k_split(const Seg* __restrict__ segs, int nA, const int32_t* __r
   const int C = nchunks_of(g.count);
   const int off = seg_off[s];
   int run = 0;
-  long long s2 = 0;
+  float s2 = 0.0f;
   for (int base = 0; base < C; base += 32) {
     int c = base + lane;
     int v = c < C ? cleft[off + c] : 0;
-    if (c < C) s2 = max(s2, cs2[off + c]);
+    if (c < C) s2 = fmaxf(s2, cs2[off + c]);
     int incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -305,8 +312,14 @@ __global__ void k_split(const Seg* __restrict__ segs, int nA, const int32_t* __r
     if (c < C) cloff[off + c] = run + incl - v;
     run += __shfl_sync(0xffffffffu, incl, 31);
   }
-  s2 = warp_max_ll(s2);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s2 = fmaxf(s2, __shfl_xor_sync(0xffffffffu, s2, o));
   if (lane != 0) return;
+  {
+    const float Dm = sqrtf(s2);
+    const float thr = Dm - 2.0f * dist_err_bound(seg_xb[s], Dm);
+    seg_thr2[s] = thr > 0.0f ? thr * thr * (1.0f - 1e-6f) : -1.0f;
+  }
   int nl = run;
   const bool fallback = (nl == 0 || nl == g.count);
   if (fallback) {
@@ -315,7 +328,6 @@ __global__ void k_split(const Seg* __restrict__ segs, int nA, const int32_t* __r
   }
   seg_nl[s] = fallback ? -nl - 1 : nl;
   const int c = g.cell;
-  A.tmp.s[c] = sqrt(__longlong_as_double(s2));
   int cid = atomicAdd(&A.counters[0], 2);
   if (cid + 2 > A.cap_cells) { set_status(A.status, ST_CAPACITY); return; }
   A.tmp.left[c] = cid;
@@ -331,7 +343,8 @@ __global__ void __launch_bounds__(kChunkThreads)
 k_chunk_scatter(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_seg,
                 const int32_t* __restrict__ seg_off, const int32_t* __restrict__ counters, PCols src,
                 PCols dst, const int32_t* __restrict__ seg_axis, const double* __restrict__ seg_cut,
-                const int32_t* __restrict__ cloff, const int32_t* __restrict__ seg_nl) {
+                const int32_t* __restrict__ cloff, const int32_t* __restrict__ seg_nl,
+                TmpCells tmp, const float* __restrict__ seg_thr2, long long* __restrict__ seg_s2) {
   const int b = blockIdx.x;
   if (b >= counters[4]) return;
   const int s = chunk_seg[b];
@@ -341,16 +354,21 @@ k_chunk_scatter(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_
   const bool fallback = code < 0;
   const int nl = fallback ? -code - 1 : code;
   const int axis = seg_axis[s];
-  const double cut = seg_cut[s];
+  const long long ckey = dkey(seg_cut[s]);
   int lefts_before = fallback ? min(rel0, nl) : cloff[b];
   __shared__ int wcount[kChunkThreads / 32];
+  __shared__ long long ws2[kChunkThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const double cx = tmp.cx[g.cell], cy = tmp.cy[g.cell], cz = tmp.cz[g.cell];
+  const float cxf = trunc_to_float(cx), cyf = trunc_to_float(cy), czf = trunc_to_float(cz);
+  const float thr2 = seg_thr2[s];
+  long long s2 = 0;
   for (int pass = 0; pass < kChunk / kChunkThreads; ++pass) {
     const int k = rel0 + pass * kChunkThreads + threadIdx.x;   // position within the segment
     const bool valid = k < g.count;
     const int64_t i = (int64_t)g.first + k;
     bool flag = false;
-    if (valid) flag = fallback ? (k < nl) : (coord(src, axis, i) < cut);
+    if (valid) flag = fallback ? (k < nl) : (dkey(coord(src, axis, i)) < ckey);
     unsigned mask = __ballot_sync(0xffffffffu, flag);
     int rank = __popc(mask & ((1u << lane) - 1u));
     if (lane == 0) wcount[w] = __popc(mask);
@@ -363,12 +381,32 @@ k_chunk_scatter(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_
     if (valid) {
       const int lb = lefts_before + woff + rank;             // left particles before k
       const int64_t d = flag ? (int64_t)g.first + lb : (int64_t)g.first + nl + (k - lb);
-      dst.x[d] = src.x[i]; dst.y[d] = src.y[i]; dst.z[d] = src.z[i];
+      const double px = src.x[i], py = src.y[i], pz = src.z[i];
+      dst.x[d] = px; dst.y[d] = py; dst.z[d] = pz;
       dst.m[d] = src.m[i]; dst.h[d] = src.h[i]; dst.idx[d] = src.idx[i];
+      const float ex = trunc_to_float(px) - cxf, ey = trunc_to_float(py) - cyf,
+                  ez = trunc_to_float(pz) - czf;
+      if (ex * ex + ey * ey + ez * ez >= thr2)
+        s2 = max(s2, __double_as_longlong(dist2_rn(px, py, pz, cx, cy, cz)));
     }
     lefts_before += tot;
     __syncthreads();
   }
+  s2 = warp_max_ll(s2);
+  if (lane == 0) ws2[w] = s2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long m2 = 0;
+    for (int q = 0; q < kChunkThreads / 32; ++q) m2 = max(m2, ws2[q]);
+    if (m2 > 0) atomicMax(reinterpret_cast<unsigned long long*>(&seg_s2[s]), (unsigned long long)m2);
+  }
+}
+
+// Size of each phase-A cell from the exact squared maximum of its candidates.
+__global__ void k_seg_size(const Seg* __restrict__ segs, int nA, const long long* __restrict__ seg_s2,
+                           TmpCells tmp) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nA) tmp.s[segs[s].cell] = sqrt(__longlong_as_double(seg_s2[s]));
 }
 
 // ---------------------------------------------------------------------------
@@ -381,203 +419,566 @@ struct SubArgs {
   int qcap;
 };
 
-// Moments of a leaf that lives in shared memory (count <= 32): one lane per
-// particle.
-__device__ void leaf_in_smem(const SubArgs& S, const double* sx, const double* sy,
-                             const double* sz, const double* sm, const uint16_t* lidx, int lf,
-                             int cnt, int cell, int depth, int gfirst) {
-  const int lane = threadIdx.x & 31;
-  auto get = [&](int k) {
-    int q = lidx[lf + k];
-    return elem4(sm[q], sx[q], sy[q], sz[q]);
-  };
-  Sum4 v = warp_pairwise(cnt, get);
+constexpr int kBlockSeg = 256;                      // split by the whole CTA at this size
+constexpr int kSubWarps = kSubtreeThreads / 32;
+
+// Shared-memory views of one subtree: float64 particles, float32 shadows of
+// the positions (for the size filter), local index and scratch index arrays,
+// and the two segment queues.
+struct SubSmem {
+  double *x, *y, *z, *m;
+  float *xf, *yf, *zf;
+  uint16_t *idx, *scr;
+  int4* q[2];
+};
+
+__device__ __forceinline__ float dist2_f(const SubSmem& S, int q, float cx, float cy, float cz) {
+  const float dx = S.xf[q] - cx, dy = S.yf[q] - cy, dz = S.zf[q] - cz;
+  return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ float abs_bound(const double lo[3], const double hi[3]) {
+  double X = 0.0;
+  for (int d = 0; d < 3; ++d) X = fmax(X, fmax(fabs(lo[d]), fabs(hi[d])));
+  return (float)X * 1.0000005f;
+}
+
+constexpr int kThreadSeg = 64;                      // split by one thread at this size
+
+// Canonical pairwise sum of the cnt (<= 2^7) particles idx[lf..lf+cnt) by one
+// thread: a carry stack builds the perfect binary tree over the sequence
+// zero-padded to a power of two.  The padded zeros are not added: a subtree
+// of zeros contributes nothing and x + 0 = x, so folding the stack from its
+// top after the last element gives the same tree value.
+__device__ __forceinline__ Sum4 thread_pairwise(const SubSmem& L, int lf, int cnt) {
+  Sum4 st[8];
+  int top = 0;
+  for (int k = 0; k < cnt; ++k) {
+    const int q = L.idx[lf + k];
+    Sum4 e = elem4(L.m[q], L.x[q], L.y[q], L.z[q]);
+    for (int kk = k; kk & 1; kk >>= 1) e = add4(st[--top], e);
+    st[top++] = e;
+  }
+  Sum4 v = st[top - 1];
+  for (int i = top - 2; i >= 0; --i) v = add4(st[i], v);
+  return v;
+}
+
+// Exact squared size of a cell held in shared memory, by one thread: float32
+// distances over the shadow coordinates select the particles that may hold the
+// maximum, and only those are evaluated in float64.
+__device__ __forceinline__ long long thread_size2(const SubSmem& L, int lf, int cnt, double cx,
+                                                  double cy, double cz) {
+  const float cxf = (float)cx, cyf = (float)cy, czf = (float)cz;
+  float d2m = 0.0f, X = fmaxf(fabsf(cxf), fmaxf(fabsf(cyf), fabsf(czf)));
+  for (int k = 0; k < cnt; ++k) {
+    const int q = L.idx[lf + k];
+    d2m = fmaxf(d2m, dist2_f(L, q, cxf, cyf, czf));
+    X = fmaxf(X, fmaxf(fabsf(L.xf[q]), fmaxf(fabsf(L.yf[q]), fabsf(L.zf[q]))));
+  }
+  const float Dm = sqrtf(d2m);
+  const float thr = Dm - 2.0f * dist_err_bound(X * 1.0000005f, Dm);
+  const float thr2 = thr > 0.0f ? thr * thr * (1.0f - 1e-6f) : -1.0f;
+  long long s2 = 0;
+  for (int k = 0; k < cnt; ++k) {
+    const int q = L.idx[lf + k];
+    if (dist2_f(L, q, cxf, cyf, czf) >= thr2)
+      s2 = max(s2, __double_as_longlong(dist2_rn(L.x[q], L.y[q], L.z[q], cx, cy, cz)));
+  }
+  return s2;
+}
+
+// Moments of a leaf in shared memory, computed by one thread.
+__device__ void leaf_thread(const SubArgs& S, const SubSmem& L, int lf, int cnt, int cell,
+                            int depth, int gfirst) {
+  const Sum4 v = thread_pairwise(L, lf, cnt);
   const double M = v.m;
   const double cx = __ddiv_rn(v.x, M), cy = __ddiv_rn(v.y, M), cz = __ddiv_rn(v.z, M);
+  const long long s2 = thread_size2(L, lf, cnt, cx, cy, cz);
+  TmpCells t = S.A.tmp;
+  t.first[cell] = gfirst + lf; t.count[cell] = cnt; t.depth[cell] = depth;
+  t.M[cell] = M; t.cx[cell] = cx; t.cy[cell] = cy; t.cz[cell] = cz;
+  t.s[cell] = sqrt(__longlong_as_double(s2));
+  t.left[cell] = -1; t.right[cell] = -1;
+}
+
+// Queues of one level of a subtree: cells to split next, leaves to finish.
+struct Queues {
+  int* qn_next;
+  int4* q_next;
+  int* nleaf;
+  int4* leaves;
+  int leafcap;
+};
+
+// Pushes child `c` (local first, count, cell, depth) onto the queue that will
+// process it; called by one thread.
+__device__ __forceinline__ void push_local(const SubArgs& S, const Queues& Q, int4 c) {
+  if (c.y > S.A.n_leaf) {
+    int pos = atomicAdd(Q.qn_next, 1);
+    if (pos < S.qcap) Q.q_next[pos] = c; else set_status(S.A.status, ST_CAPACITY);
+  } else {
+    int pos = atomicAdd(Q.nleaf, 1);
+    if (pos < Q.leafcap) Q.leaves[pos] = c; else set_status(S.A.status, ST_CAPACITY);
+  }
+}
+
+// Allocates the two children of `cell` and queues them (lane 0 of the calling
+// warp).  Returns false if the cell table is full.
+__device__ bool make_children(const SubArgs& S, const Queues& Q, int lf, int cnt, int nl, int cell,
+                              int depth) {
+  const int lane = threadIdx.x & 31;
+  const BuildArgs& A = S.A;
+  int ok = 1;
+  if (lane == 0) {
+    const int cid = atomicAdd(&A.counters[0], 2);
+    if (cid + 2 > A.cap_cells) {
+      set_status(A.status, ST_CAPACITY);
+      ok = 0;
+    } else {
+      A.tmp.left[cell] = cid;
+      A.tmp.right[cell] = cid + 1;
+      push_local(S, Q, make_int4(lf, nl, cid, depth + 1));
+      push_local(S, Q, make_int4(lf + nl, cnt - nl, cid + 1, depth + 1));
+    }
+  }
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// A segment split by one thread (small cells): sums, bounding box, centre of
+// mass, exact size, serial stable partition; leaf children are finished at
+// once by the same thread.
+__device__ void split_thread(const SubArgs& S, const SubSmem& L, const Queues& Q, int4 e, int gfirst,
+                             int& depth_max) {
+  const int lf = e.x, cnt = e.y, cell = e.z, depth = e.w;
+  const BuildArgs& A = S.A;
+  const Sum4 v = thread_pairwise(L, lf, cnt);
+  long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+  for (int k = 0; k < cnt; ++k) {
+    const int q = L.idx[lf + k];
+    const long long kx = dkey(L.x[q]), ky = dkey(L.y[q]), kz = dkey(L.z[q]);
+    lo[0] = min(lo[0], kx); hi[0] = max(hi[0], kx);
+    lo[1] = min(lo[1], ky); hi[1] = max(hi[1], ky);
+    lo[2] = min(lo[2], kz); hi[2] = max(hi[2], kz);
+  }
+  double dlo[3], dhi[3];
+  for (int d = 0; d < 3; ++d) { dlo[d] = dunkey(lo[d]); dhi[d] = dunkey(hi[d]); }
+  const double M = v.m;
+  const double cx = __ddiv_rn(v.x, M), cy = __ddiv_rn(v.y, M), cz = __ddiv_rn(v.z, M);
+  const int axis = longest_axis(dlo, dhi);
+  const long long ckey = dkey(axis == 0 ? cx : (axis == 1 ? cy : cz));
+  const double* sa = axis == 0 ? L.x : (axis == 1 ? L.y : L.z);
+  const long long s2 = thread_size2(L, lf, cnt, cx, cy, cz);
+  int nl = 0;
+  for (int k = 0; k < cnt; ++k) nl += dkey(sa[L.idx[lf + k]]) < ckey;
+  if (nl == 0 || nl == cnt) {
+    nl = cnt / 2;
+    atomicAdd(&A.counters[5], 1);
+  } else {
+    int l = 0, r = nl;
+    for (int k = 0; k < cnt; ++k) {
+      const int q = L.idx[lf + k];
+      L.scr[lf + (dkey(sa[q]) < ckey ? l++ : r++)] = (uint16_t)q;
+    }
+    for (int k = 0; k < cnt; ++k) L.idx[lf + k] = L.scr[lf + k];
+  }
+  TmpCells t = A.tmp;
+  t.first[cell] = gfirst + lf; t.count[cell] = cnt; t.depth[cell] = depth;
+  t.M[cell] = M; t.cx[cell] = cx; t.cy[cell] = cy; t.cz[cell] = cz;
+  t.s[cell] = sqrt(__longlong_as_double(s2));
+  const int cid = atomicAdd(&A.counters[0], 2);
+  if (cid + 2 > A.cap_cells) {
+    set_status(A.status, ST_CAPACITY);
+    return;
+  }
+  t.left[cell] = cid;
+  t.right[cell] = cid + 1;
+  depth_max = max(depth_max, depth + 1);
+  const int clf[2] = {lf, lf + nl}, ccnt[2] = {nl, cnt - nl};
+  for (int side = 0; side < 2; ++side) {
+    if (ccnt[side] > A.n_leaf) {
+      int pos = atomicAdd(Q.qn_next, 1);
+      if (pos < S.qcap) Q.q_next[pos] = make_int4(clf[side], ccnt[side], cid + side, depth + 1);
+      else set_status(A.status, ST_CAPACITY);
+    } else {
+      leaf_thread(S, L, clf[side], ccnt[side], cid + side, depth + 1, gfirst);
+    }
+  }
+}
+
+// A segment split by one warp.
+__device__ void split_warp(const SubArgs& S, const SubSmem& L, const Queues& Q, int4 e, int gfirst,
+                           int& depth_max) {
+  const int lane = threadIdx.x & 31;
+  const int lf = e.x, cnt = e.y, cell = e.z, depth = e.w;
+  const BuildArgs& A = S.A;
+  auto get = [&](int k) {
+    int qq = L.idx[lf + k];
+    return elem4(L.m[qq], L.x[qq], L.y[qq], L.z[qq]);
+  };
+  Sum4 v = warp_pairwise(cnt, get);
+  long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+  for (int k = lane; k < cnt; k += 32) {
+    int qq = L.idx[lf + k];
+    long long kx = dkey(L.x[qq]), ky = dkey(L.y[qq]), kz = dkey(L.z[qq]);
+    lo[0] = min(lo[0], kx); hi[0] = max(hi[0], kx);
+    lo[1] = min(lo[1], ky); hi[1] = max(hi[1], ky);
+    lo[2] = min(lo[2], kz); hi[2] = max(hi[2], kz);
+  }
+  double dlo[3], dhi[3];
+  for (int d = 0; d < 3; ++d) { dlo[d] = dunkey(warp_min_ll(lo[d])); dhi[d] = dunkey(warp_max_ll(hi[d])); }
+  const double M = v.m;
+  // the three divisions run once, on lanes 0, 1, 2
+  const double quo = __ddiv_rn(lane == 1 ? v.y : (lane == 2 ? v.z : v.x), M);
+  const double cx = __shfl_sync(0xffffffffu, quo, 0), cy = __shfl_sync(0xffffffffu, quo, 1),
+               cz = __shfl_sync(0xffffffffu, quo, 2);
+  const int axis = longest_axis(dlo, dhi);
+  const long long ckey = dkey(axis == 0 ? cx : (axis == 1 ? cy : cz));
+  const double* sa = axis == 0 ? L.x : (axis == 1 ? L.y : L.z);
+  // size: float32 filter, then exact float64 for the candidates
+  const float cxf = (float)cx, cyf = (float)cy, czf = (float)cz, X = abs_bound(dlo, dhi);
+  float d2m = 0.0f;
+  int nl = 0;
+  for (int k = lane; k < cnt; k += 32) {
+    int qq = L.idx[lf + k];
+    d2m = fmaxf(d2m, dist2_f(L, qq, cxf, cyf, czf));
+    nl += dkey(sa[qq]) < ckey;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    d2m = fmaxf(d2m, __shfl_xor_sync(0xffffffffu, d2m, o));
+    nl += __shfl_xor_sync(0xffffffffu, nl, o);
+  }
+  const float Dm = sqrtf(d2m);
+  const float thr = Dm - 2.0f * dist_err_bound(X, Dm);
+  const float thr2 = thr > 0.0f ? thr * thr * (1.0f - 1e-6f) : -1.0f;
   long long s2 = 0;
-  if (lane < cnt) {
-    int q = lidx[lf + lane];
-    s2 = __double_as_longlong(dist2_rn(sx[q], sy[q], sz[q], cx, cy, cz));
+  for (int k = lane; k < cnt; k += 32) {
+    int qq = L.idx[lf + k];
+    if (dist2_f(L, qq, cxf, cyf, czf) >= thr2)
+      s2 = max(s2, __double_as_longlong(dist2_rn(L.x[qq], L.y[qq], L.z[qq], cx, cy, cz)));
   }
   s2 = warp_max_ll(s2);
+  const bool fallback = (nl == 0 || nl == cnt);
+  if (fallback) {
+    nl = cnt / 2;
+    if (lane == 0) atomicAdd(&A.counters[5], 1);
+  } else {
+    int offl = 0, offr = nl;
+    for (int base = 0; base < cnt; base += 32) {
+      int k = base + lane;
+      bool valid = k < cnt;
+      int qq = valid ? L.idx[lf + k] : 0;
+      bool f = valid && dkey(sa[qq]) < ckey;
+      unsigned ml = __ballot_sync(0xffffffffu, f);
+      unsigned mr = __ballot_sync(0xffffffffu, valid && !f);
+      unsigned lt = (1u << lane) - 1u;
+      if (valid) L.scr[lf + (f ? offl + __popc(ml & lt) : offr + __popc(mr & lt))] = (uint16_t)qq;
+      offl += __popc(ml);
+      offr += __popc(mr);
+    }
+    __syncwarp();
+    for (int k = lane; k < cnt; k += 32) L.idx[lf + k] = L.scr[lf + k];
+    __syncwarp();
+  }
   if (lane == 0) {
-    TmpCells t = S.A.tmp;
+    TmpCells t = A.tmp;
     t.first[cell] = gfirst + lf; t.count[cell] = cnt; t.depth[cell] = depth;
     t.M[cell] = M; t.cx[cell] = cx; t.cy[cell] = cy; t.cz[cell] = cz;
     t.s[cell] = sqrt(__longlong_as_double(s2));
-    t.left[cell] = -1; t.right[cell] = -1;
   }
+  if (make_children(S, Q, lf, cnt, nl, cell, depth)) depth_max = max(depth_max, depth + 1);
+}
+
+// Block-wide helpers (all kSubtreeThreads threads call them).
+struct BlockScratch {
+  Sum4 ws[kSubWarps];
+  long long wk[kSubWarps][6];
+  float wf[kSubWarps];
+  int wi[kSubWarps];
+  double com[3];
+  double bb[6];
+  float thr2;
+  int nl;
+  int axis;
+};
+
+// A segment split by the whole CTA.  The pairwise sum splits the padded
+// sequence into kSubWarps aligned sub-blocks, one per warp (the top levels of
+// the same perfect tree).
+__device__ void split_block(const SubArgs& S, const SubSmem& L, BlockScratch& B, const Queues& Q,
+                            int4 e, int gfirst, int& depth_max) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lf = e.x, cnt = e.y, cell = e.z, depth = e.w;
+  const BuildArgs& A = S.A;
+  int P = 1;
+  while (P < cnt) P <<= 1;                         // P >= kBlockSeg = 256
+  const int Pw = P / kSubWarps;                    // per warp, >= 32
+  const int base = w * Pw + lane * (Pw >> 5);
+  auto get = [&](int k) {
+    int qq = L.idx[lf + k];
+    return elem4(L.m[qq], L.x[qq], L.y[qq], L.z[qq]);
+  };
+  Sum4 v;
+  switch (Pw >> 5) {
+    case 1: v = block_tree<0>(base, cnt, get); break;
+    case 2: v = block_tree<1>(base, cnt, get); break;
+    case 4: v = block_tree<2>(base, cnt, get); break;
+    default: v = block_tree<3>(base, cnt, get); break;
+  }
+  v = warp_tree4(v);
+  long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+  for (int k = threadIdx.x; k < cnt; k += kSubtreeThreads) {
+    int qq = L.idx[lf + k];
+    long long kx = dkey(L.x[qq]), ky = dkey(L.y[qq]), kz = dkey(L.z[qq]);
+    lo[0] = min(lo[0], kx); hi[0] = max(hi[0], kx);
+    lo[1] = min(lo[1], ky); hi[1] = max(hi[1], ky);
+    lo[2] = min(lo[2], kz); hi[2] = max(hi[2], kz);
+  }
+  for (int d = 0; d < 3; ++d) { lo[d] = warp_min_ll(lo[d]); hi[d] = warp_max_ll(hi[d]); }
+  if (lane == 0) {
+    B.ws[w] = v;
+    for (int d = 0; d < 3; ++d) { B.wk[w][d] = lo[d]; B.wk[w][3 + d] = hi[d]; }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Sum4 t = add4(add4(add4(B.ws[0], B.ws[1]), add4(B.ws[2], B.ws[3])),
+                  add4(add4(B.ws[4], B.ws[5]), add4(B.ws[6], B.ws[7])));
+    double dlo[3], dhi[3];
+    for (int d = 0; d < 3; ++d) {
+      long long l = B.wk[0][d], h = B.wk[0][3 + d];
+      for (int q = 1; q < kSubWarps; ++q) { l = min(l, B.wk[q][d]); h = max(h, B.wk[q][3 + d]); }
+      dlo[d] = dunkey(l);
+      dhi[d] = dunkey(h);
+    }
+    B.com[0] = t.x; B.com[1] = t.y; B.com[2] = t.z; B.bb[0] = t.m;
+    B.axis = longest_axis(dlo, dhi);
+  }
+  __syncthreads();
+  if (w == 0) {                                    // the three divisions on lanes 0, 1, 2
+    const double quo = __ddiv_rn(B.com[lane < 3 ? lane : 0], B.bb[0]);
+    const double Mc = B.bb[0];
+    __syncwarp();
+    if (lane < 3) B.com[lane] = quo;
+    if (lane == 0) {
+      TmpCells tc = A.tmp;
+      tc.first[cell] = gfirst + lf; tc.count[cell] = cnt; tc.depth[cell] = depth;
+      tc.M[cell] = Mc; tc.cx[cell] = quo;
+    }
+    const double qy = __shfl_sync(0xffffffffu, quo, 1), qz = __shfl_sync(0xffffffffu, quo, 2);
+    if (lane == 0) { A.tmp.cy[cell] = qy; A.tmp.cz[cell] = qz; }
+  }
+  __syncthreads();
+  const double cx = B.com[0], cy = B.com[1], cz = B.com[2];
+  const int axis = B.axis;
+  const long long ckey = dkey(B.com[axis]);
+  const double* sa = axis == 0 ? L.x : (axis == 1 ? L.y : L.z);
+  const float cxf = (float)cx, cyf = (float)cy, czf = (float)cz;
+  float d2m = 0.0f;
+  int nl = 0;
+  for (int k = threadIdx.x; k < cnt; k += kSubtreeThreads) {
+    int qq = L.idx[lf + k];
+    d2m = fmaxf(d2m, dist2_f(L, qq, cxf, cyf, czf));
+    nl += dkey(sa[qq]) < ckey;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    d2m = fmaxf(d2m, __shfl_xor_sync(0xffffffffu, d2m, o));
+    nl += __shfl_xor_sync(0xffffffffu, nl, o);
+  }
+  if (lane == 0) { B.wf[w] = d2m; B.wi[w] = nl; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m2 = 0.0f;
+    int t = 0;
+    for (int q = 0; q < kSubWarps; ++q) { m2 = fmaxf(m2, B.wf[q]); t += B.wi[q]; }
+    double blo[3], bhi[3];
+    for (int d = 0; d < 3; ++d) {
+      long long l = B.wk[0][d], h = B.wk[0][3 + d];
+      for (int q = 1; q < kSubWarps; ++q) { l = min(l, B.wk[q][d]); h = max(h, B.wk[q][3 + d]); }
+      blo[d] = dunkey(l);
+      bhi[d] = dunkey(h);
+    }
+    const float Dm = sqrtf(m2);
+    const float thr = Dm - 2.0f * dist_err_bound(abs_bound(blo, bhi), Dm);
+    B.thr2 = thr > 0.0f ? thr * thr * (1.0f - 1e-6f) : -1.0f;
+    B.nl = t;
+  }
+  __syncthreads();
+  const float thr2 = B.thr2;
+  nl = B.nl;
+  long long s2 = 0;
+  for (int k = threadIdx.x; k < cnt; k += kSubtreeThreads) {
+    int qq = L.idx[lf + k];
+    if (dist2_f(L, qq, cxf, cyf, czf) >= thr2)
+      s2 = max(s2, __double_as_longlong(dist2_rn(L.x[qq], L.y[qq], L.z[qq], cx, cy, cz)));
+  }
+  s2 = warp_max_ll(s2);
+  __syncthreads();                                 // B.wk reused below
+  if (lane == 0) B.wk[w][0] = s2;
+  const bool fallback = (nl == 0 || nl == cnt);
+  if (!fallback) {
+    // stable partition in rounds of one element per thread
+    int offl = 0;
+    for (int r0 = 0; r0 < cnt; r0 += kSubtreeThreads) {
+      const int k = r0 + threadIdx.x;
+      const bool valid = k < cnt;
+      const int qq = valid ? L.idx[lf + k] : 0;
+      const bool f = valid && dkey(sa[qq]) < ckey;
+      const unsigned ml = __ballot_sync(0xffffffffu, f);
+      if (lane == 0) B.wi[w] = __popc(ml);
+      __syncthreads();
+      int woff = 0, tot = 0;
+      for (int q = 0; q < kSubWarps; ++q) {
+        if (q < w) woff += B.wi[q];
+        tot += B.wi[q];
+      }
+      if (valid) {
+        const int lb = offl + woff + __popc(ml & ((1u << lane) - 1u));
+        L.scr[lf + (f ? lb : nl + (k - lb))] = (uint16_t)qq;
+      }
+      offl += tot;
+      __syncthreads();
+    }
+    for (int k = threadIdx.x; k < cnt; k += kSubtreeThreads) L.idx[lf + k] = L.scr[lf + k];
+  }
+  __syncthreads();
+  if (w == 0) {
+    long long m2 = lane < kSubWarps ? B.wk[lane][0] : 0;
+    m2 = warp_max_ll(m2);
+    if (lane == 0) A.tmp.s[cell] = sqrt(__longlong_as_double(m2));
+    if (fallback) {
+      nl = cnt / 2;
+      if (lane == 0) atomicAdd(&A.counters[5], 1);
+    }
+    if (make_children(S, Q, lf, cnt, nl, cell, depth)) depth_max = max(depth_max, depth + 1);
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kSubtreeThreads)
 k_subtree(SubArgs S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sx = reinterpret_cast<double*>(smem_raw);
-  double* sy = sx + kSubtreeMax;
-  double* sz = sy + kSubtreeMax;
-  double* sm = sz + kSubtreeMax;
-  uint16_t* lidx = reinterpret_cast<uint16_t*>(sm + kSubtreeMax);
-  uint16_t* lscr = lidx + kSubtreeMax;
-  int4* q[2];
-  q[0] = reinterpret_cast<int4*>(lscr + kSubtreeMax);
-  q[1] = q[0] + S.qcap;
+  __shared__ BlockScratch B;
   __shared__ int qn[2];
+  __shared__ int nleaf;
+  SubSmem L;
+  L.x = reinterpret_cast<double*>(smem_raw);
+  L.y = L.x + kSubtreeMax;
+  L.z = L.y + kSubtreeMax;
+  L.m = L.z + kSubtreeMax;
+  L.xf = reinterpret_cast<float*>(L.m + kSubtreeMax);
+  L.yf = L.xf + kSubtreeMax;
+  L.zf = L.yf + kSubtreeMax;
+  L.idx = reinterpret_cast<uint16_t*>(L.zf + kSubtreeMax);
+  L.scr = L.idx + kSubtreeMax;
+  L.q[0] = reinterpret_cast<int4*>(L.scr + kSubtreeMax);
+  L.q[1] = L.q[0] + S.qcap;
+  int4* leaves = L.q[1] + S.qcap;
+  const int leafcap = 2 * S.qcap;
 
   const Seg g = S.segB[blockIdx.x];
   const PCols in = (g.dbuf & 1) ? S.buf1 : S.buf0;
   const int n = g.count;
   const int gfirst = g.first;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    sx[k] = in.x[gfirst + k]; sy[k] = in.y[gfirst + k]; sz[k] = in.z[gfirst + k];
-    sm[k] = in.m[gfirst + k];
-    lidx[k] = (uint16_t)k;
+    const double x = in.x[gfirst + k], y = in.y[gfirst + k], z = in.z[gfirst + k];
+    L.x[k] = x; L.y[k] = y; L.z[k] = z;
+    L.m[k] = in.m[gfirst + k];
+    L.xf[k] = trunc_to_float(x); L.yf[k] = trunc_to_float(y); L.zf[k] = trunc_to_float(z);
+    L.idx[k] = (uint16_t)k;
   }
   int cur = 0;
   if (threadIdx.x == 0) {
-    q[0][0] = make_int4(0, n, g.cell, g.dbuf >> 1);
+    L.q[0][0] = make_int4(0, n, g.cell, g.dbuf >> 1);
     qn[0] = 1;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const BuildArgs& A = S.A;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   int depth_max = 0;
   while (qn[cur] > 0) {
     const int nxt = cur ^ 1;
-    if (threadIdx.x == 0) qn[nxt] = 0;
+    if (threadIdx.x == 0) { qn[nxt] = 0; nleaf = 0; }
     __syncthreads();
     const int nq = qn[cur];
+    const Queues Q{&qn[nxt], L.q[nxt], &nleaf, leaves, leafcap};
+    // large cells: the whole CTA, one after the other
+    for (int qi = 0; qi < nq; ++qi) {
+      const int4 e = L.q[cur][qi];
+      if (e.y >= kBlockSeg) split_block(S, L, B, Q, e, gfirst, depth_max);
+    }
+    // medium cells: one warp each
     for (int qi = warp; qi < nq; qi += nwarps) {
-      const int4 e = q[cur][qi];
-      const int lf = e.x, cnt = e.y, cell = e.z, depth = e.w;
-      auto get = [&](int k) {
-        int qq = lidx[lf + k];
-        return elem4(sm[qq], sx[qq], sy[qq], sz[qq]);
-      };
-      Sum4 v = warp_pairwise(cnt, get);
-      long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
-      for (int k = lane; k < cnt; k += 32) {
-        int qq = lidx[lf + k];
-        long long kx = dkey(sx[qq]), ky = dkey(sy[qq]), kz = dkey(sz[qq]);
-        lo[0] = min(lo[0], kx); hi[0] = max(hi[0], kx);
-        lo[1] = min(lo[1], ky); hi[1] = max(hi[1], ky);
-        lo[2] = min(lo[2], kz); hi[2] = max(hi[2], kz);
-      }
-      double dlo[3], dhi[3];
-      for (int d = 0; d < 3; ++d) { dlo[d] = dunkey(warp_min_ll(lo[d])); dhi[d] = dunkey(warp_max_ll(hi[d])); }
-      const double M = v.m;
-      const double cx = __ddiv_rn(v.x, M), cy = __ddiv_rn(v.y, M), cz = __ddiv_rn(v.z, M);
-      const int axis = longest_axis(dlo, dhi);
-      const double cut = axis == 0 ? cx : (axis == 1 ? cy : cz);
-      const double* sa = axis == 0 ? sx : (axis == 1 ? sy : sz);
-      // exact size and the number of particles left of the cut
-      long long s2 = 0;
-      int nl = 0;
-      for (int k = lane; k < cnt; k += 32) {
-        int qq = lidx[lf + k];
-        s2 = max(s2, __double_as_longlong(dist2_rn(sx[qq], sy[qq], sz[qq], cx, cy, cz)));
-        nl += sa[qq] < cut;
-      }
-      s2 = warp_max_ll(s2);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) nl += __shfl_xor_sync(0xffffffffu, nl, o);
-      const bool fallback = (nl == 0 || nl == cnt);
-      if (fallback) {
-        nl = cnt / 2;
-        if (lane == 0) atomicAdd(&A.counters[5], 1);
-      } else {
-        // stable partition through the scratch index array
-        int offl = 0, offr = nl;
-        for (int base = 0; base < cnt; base += 32) {
-          int k = base + lane;
-          bool valid = k < cnt;
-          int qq = valid ? lidx[lf + k] : 0;
-          bool f = valid && sa[qq] < cut;
-          unsigned ml = __ballot_sync(0xffffffffu, f);
-          unsigned mr = __ballot_sync(0xffffffffu, valid && !f);
-          unsigned lt = (1u << lane) - 1u;
-          if (valid) lscr[lf + (f ? offl + __popc(ml & lt) : offr + __popc(mr & lt))] = (uint16_t)qq;
-          offl += __popc(ml);
-          offr += __popc(mr);
-        }
-        __syncwarp();
-        for (int k = lane; k < cnt; k += 32) lidx[lf + k] = lscr[lf + k];
-        __syncwarp();
-      }
-      int cid = 0;
-      if (lane == 0) {
-        TmpCells t = A.tmp;
-        t.first[cell] = gfirst + lf; t.count[cell] = cnt; t.depth[cell] = depth;
-        t.M[cell] = M; t.cx[cell] = cx; t.cy[cell] = cy; t.cz[cell] = cz;
-        t.s[cell] = sqrt(__longlong_as_double(s2));
-        cid = atomicAdd(&A.counters[0], 2);
-        if (cid + 2 > A.cap_cells) {
-          set_status(A.status, ST_CAPACITY);
-          cid = -1;
-        } else {
-          t.left[cell] = cid;
-          t.right[cell] = cid + 1;
-        }
-      }
-      cid = __shfl_sync(0xffffffffu, cid, 0);
-      if (cid < 0) continue;
-      depth_max = max(depth_max, depth + 1);
-      const int clf[2] = {lf, lf + nl}, ccnt[2] = {nl, cnt - nl};
-      for (int side = 0; side < 2; ++side) {
-        if (ccnt[side] > A.n_leaf) {
-          if (lane == 0) {
-            int pos = atomicAdd(&qn[nxt], 1);
-            if (pos < S.qcap) q[nxt][pos] = make_int4(clf[side], ccnt[side], cid + side, depth + 1);
-            else set_status(A.status, ST_CAPACITY);
-          }
-        } else {
-          leaf_in_smem(S, sx, sy, sz, sm, lidx, clf[side], ccnt[side], cid + side, depth + 1, gfirst);
-        }
-      }
+      const int4 e = L.q[cur][qi];
+      if (e.y > kThreadSeg && e.y < kBlockSeg) split_warp(S, L, Q, e, gfirst, depth_max);
+    }
+    // small cells: one thread each (with their leaf children)
+    for (int qi = threadIdx.x; qi < nq; qi += blockDim.x) {
+      const int4 e = L.q[cur][qi];
+      if (e.y <= kThreadSeg) split_thread(S, L, Q, e, gfirst, depth_max);
+    }
+    __syncthreads();
+    // leaves split off by the CTA and warp passes: one thread each
+    const int nlv = min(nleaf, leafcap);
+    for (int li = threadIdx.x; li < nlv; li += blockDim.x) {
+      const int4 e = leaves[li];
+      leaf_thread(S, L, e.x, e.y, e.z, e.w, gfirst);
     }
     __syncthreads();
     cur ^= 1;
   }
-  if (lane == 0 && depth_max > 0) atomicMax(&A.counters[6], depth_max);
+  depth_max = max(depth_max, __shfl_xor_sync(0xffffffffu, depth_max, 16));
+  depth_max = max(depth_max, __shfl_xor_sync(0xffffffffu, depth_max, 8));
+  depth_max = max(depth_max, __shfl_xor_sync(0xffffffffu, depth_max, 4));
+  depth_max = max(depth_max, __shfl_xor_sync(0xffffffffu, depth_max, 2));
+  depth_max = max(depth_max, __shfl_xor_sync(0xffffffffu, depth_max, 1));
+  if ((threadIdx.x & 31) == 0 && depth_max > 0) atomicMax(&S.A.counters[6], depth_max);
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    int src = lidx[k];
+    int src = L.idx[k];
     int64_t p = (int64_t)gfirst + k;
-    S.out.x[p] = sx[src]; S.out.y[p] = sy[src]; S.out.z[p] = sz[src]; S.out.m[p] = sm[src];
+    S.out.x[p] = L.x[src]; S.out.y[p] = L.y[src]; S.out.z[p] = L.z[src]; S.out.m[p] = L.m[src];
     S.out.h[p] = in.h[gfirst + src];
     S.out.idx[p] = in.idx[gfirst + src];
   }
 }
 
-// Leaves produced directly by phase A (or a root that is already a leaf).
+// Leaves produced directly by phase A (or a root that is already a leaf): one
+// thread per leaf, pairwise sums by a carry stack.
 __global__ void k_leaf_segs(SubArgs S, const Seg* __restrict__ segL, int nL) {
-  const int sidx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int sidx = blockIdx.x * blockDim.x + threadIdx.x;
   if (sidx >= nL) return;
   const Seg g = segL[sidx];
   const PCols in = (g.dbuf & 1) ? S.buf1 : S.buf0;
   const int cnt = g.count;
-  auto get = [&](int k) {
-    int64_t i = (int64_t)g.first + k;
-    return elem4(in.m[i], in.x[i], in.y[i], in.z[i]);
-  };
-  Sum4 v = warp_pairwise(cnt, get);
+  int P = 1;
+  while (P < cnt) P <<= 1;
+  Sum4 st[8];
+  int top = 0;
+  for (int k = 0; k < P; ++k) {
+    Sum4 e = zero4();
+    if (k < cnt) {
+      const int64_t i = (int64_t)g.first + k;
+      e = elem4(in.m[i], in.x[i], in.y[i], in.z[i]);
+    }
+    for (int kk = k; kk & 1; kk >>= 1) e = add4(st[--top], e);
+    st[top++] = e;
+  }
+  const Sum4 v = st[0];
   const double M = v.m;
   const double cx = __ddiv_rn(v.x, M), cy = __ddiv_rn(v.y, M), cz = __ddiv_rn(v.z, M);
   long long s2 = 0;
-  if (lane < cnt) {
-    int64_t i = (int64_t)g.first + lane;
-    s2 = __double_as_longlong(dist2_rn(in.x[i], in.y[i], in.z[i], cx, cy, cz));
+  for (int k = 0; k < cnt; ++k) {
+    const int64_t i = (int64_t)g.first + k;
+    s2 = max(s2, __double_as_longlong(dist2_rn(in.x[i], in.y[i], in.z[i], cx, cy, cz)));
     S.out.x[i] = in.x[i]; S.out.y[i] = in.y[i]; S.out.z[i] = in.z[i];
     S.out.m[i] = in.m[i]; S.out.h[i] = in.h[i]; S.out.idx[i] = in.idx[i];
   }
-  s2 = warp_max_ll(s2);
-  if (lane == 0) {
-    TmpCells t = S.A.tmp;
-    const int c = g.cell;
-    t.first[c] = g.first; t.count[c] = cnt; t.depth[c] = g.dbuf >> 1;
-    t.M[c] = M; t.cx[c] = cx; t.cy[c] = cy; t.cz[c] = cz;
-    t.s[c] = sqrt(__longlong_as_double(s2));
-    t.left[c] = -1; t.right[c] = -1;
-  }
+  TmpCells t = S.A.tmp;
+  const int c = g.cell;
+  t.first[c] = g.first; t.count[c] = cnt; t.depth[c] = g.dbuf >> 1;
+  t.M[c] = M; t.cx[c] = cx; t.cy[c] = cy; t.cz[c] = cz;
+  t.s[c] = sqrt(__longlong_as_double(s2));
+  t.left[c] = -1; t.right[c] = -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -626,20 +1027,22 @@ __global__ void k_remap(TmpCells tmp, int ncells, const int32_t* __restrict__ st
   if (id == 0) c.parent[0] = -1;
 }
 
-// Leaves: h_max and Q (Eq. 7) from their particles; then each parent, once its
-// second child has finished, from its children (parallel-axis shift of Q).
-__global__ void k_upward(Cells c, int ncells, PCols tp) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ncells || c.left[t] >= 0) return;
+// Leaves: h_max and Q (Eq. 7) from their particles (one thread per leaf);
+// then each parent, once its second child has finished, from its children
+// (parallel-axis shift of Q).  Every sum runs in a fixed order.
+__global__ void k_upward(Cells c, const int32_t* __restrict__ leaf_cells, int nleaves, PCols tp) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nleaves) return;
+  const int t = leaf_cells[k];
+  double q[6] = {0, 0, 0, 0, 0, 0}, hm = 0.0;
   {
     const int f = c.first[t], cnt = c.count[t];
     const double cx = c.cx[t], cy = c.cy[t], cz = c.cz[t];
-    double q[6] = {0, 0, 0, 0, 0, 0}, hm = 0.0;
-    for (int k = 0; k < cnt; ++k) {
-      int64_t i = (int64_t)f + k;
-      double m = tp.m[i];
-      double y0 = tp.x[i] - cx, y1 = tp.y[i] - cy, y2 = tp.z[i] - cz;
-      double y2s = y0 * y0 + y1 * y1 + y2 * y2;
+    for (int j = 0; j < cnt; ++j) {
+      const int64_t i = (int64_t)f + j;
+      const double m = tp.m[i];
+      const double y0 = tp.x[i] - cx, y1 = tp.y[i] - cy, y2 = tp.z[i] - cz;
+      const double y2s = y0 * y0 + y1 * y1 + y2 * y2;
       q[0] += m * (3.0 * y0 * y0 - y2s);
       q[1] += m * (3.0 * y0 * y1);
       q[2] += m * (3.0 * y0 * y2);
@@ -648,9 +1051,9 @@ __global__ void k_upward(Cells c, int ncells, PCols tp) {
       q[5] += m * (3.0 * y2 * y2 - y2s);
       hm = fmax(hm, tp.h[i]);
     }
-    for (int k = 0; k < 6; ++k) c.Q[6 * t + k] = q[k];
-    c.hmax[t] = hm;
   }
+  for (int j = 0; j < 6; ++j) c.Q[6 * t + j] = q[j];
+  c.hmax[t] = hm;
   int cur = t;
   while (true) {
     const int p = c.parent[cur];
@@ -659,29 +1062,34 @@ __global__ void k_upward(Cells c, int ncells, PCols tp) {
     if (atomicAdd(&c.ready[p], 1) == 0) break;      // the sibling finishes the parent
     __threadfence();
     const double px = c.cx[p], py = c.cy[p], pz = c.cz[p];
-    double q[6] = {0, 0, 0, 0, 0, 0}, hm = 0.0;
+    double qp[6] = {0, 0, 0, 0, 0, 0}, hp = 0.0;
     const int ch[2] = {c.left[p], c.right[p]};
     for (int side = 0; side < 2; ++side) {
-      const int k = ch[side];
-      const double mk = c.M[k];
-      const double d0 = c.cx[k] - px, d1 = c.cy[k] - py, d2 = c.cz[k] - pz;
+      const int kc = ch[side];
+      const double mk = c.M[kc];
+      const double d0 = c.cx[kc] - px, d1 = c.cy[kc] - py, d2 = c.cz[kc] - pz;
       const double dd = d0 * d0 + d1 * d1 + d2 * d2;
-      q[0] += __ldcg(&c.Q[6 * k + 0]) + mk * (3.0 * d0 * d0 - dd);
-      q[1] += __ldcg(&c.Q[6 * k + 1]) + mk * (3.0 * d0 * d1);
-      q[2] += __ldcg(&c.Q[6 * k + 2]) + mk * (3.0 * d0 * d2);
-      q[3] += __ldcg(&c.Q[6 * k + 3]) + mk * (3.0 * d1 * d1 - dd);
-      q[4] += __ldcg(&c.Q[6 * k + 4]) + mk * (3.0 * d1 * d2);
-      q[5] += __ldcg(&c.Q[6 * k + 5]) + mk * (3.0 * d2 * d2 - dd);
-      hm = fmax(hm, __ldcg(&c.hmax[k]));
+      qp[0] += __ldcg(&c.Q[6 * kc + 0]) + mk * (3.0 * d0 * d0 - dd);
+      qp[1] += __ldcg(&c.Q[6 * kc + 1]) + mk * (3.0 * d0 * d1);
+      qp[2] += __ldcg(&c.Q[6 * kc + 2]) + mk * (3.0 * d0 * d2);
+      qp[3] += __ldcg(&c.Q[6 * kc + 3]) + mk * (3.0 * d1 * d1 - dd);
+      qp[4] += __ldcg(&c.Q[6 * kc + 4]) + mk * (3.0 * d1 * d2);
+      qp[5] += __ldcg(&c.Q[6 * kc + 5]) + mk * (3.0 * d2 * d2 - dd);
+      hp = fmax(hp, __ldcg(&c.hmax[kc]));
     }
-    for (int k = 0; k < 6; ++k) c.Q[6 * p + k] = q[k];
-    c.hmax[p] = hm;
+    for (int j = 0; j < 6; ++j) c.Q[6 * p + j] = qp[j];
+    c.hmax[p] = hp;
     cur = p;
   }
 }
 
-// float32 views of the cells; leaf flags for the leaf ranking.
-__global__ void k_derive_cells(Cells c, int ncells, int32_t* leaf_flag, float* com_bound) {
+__global__ void k_leaf_flags(const Cells c, int ncells, int32_t* flag) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ncells) flag[t] = c.left[t] < 0 ? 1 : 0;
+}
+
+// float32 views of the cells.
+__global__ void k_derive_cells(Cells c, int ncells, float* com_bound) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ncells) return;
   const double cx = c.cx[t], cy = c.cy[t], cz = c.cz[t];
@@ -697,7 +1105,6 @@ __global__ void k_derive_cells(Cells c, int ncells, int32_t* leaf_flag, float* c
   double* s64 = c.src64 + 10 * (int64_t)t;
   s64[0] = cx; s64[1] = cy; s64[2] = cz; s64[3] = c.M[t];
   for (int k = 0; k < 6; ++k) s64[4 + k] = c.Q[6 * t + k];
-  leaf_flag[t] = c.left[t] < 0 ? 1 : 0;
   float b = fmaxf(fabsf((float)cx), fmaxf(fabsf((float)cy), fabsf((float)cz)));
   atomicMax(reinterpret_cast<int*>(com_bound), __float_as_int(b));
 }
@@ -752,6 +1159,7 @@ void free_build_buffers(kdfmm_tree_s* t) {
   free_cols(&t->tp);
   void* ptrs[] = {t->segB, t->segL, t->chunk_seg, t->seg_chunk_off, t->chunk_sum, t->chunk_key,
                   t->chunk_left, t->chunk_loff, t->chunk_s2, t->seg_axis, t->seg_cut, t->seg_nl,
+                  t->seg_xb, t->seg_thr2, t->seg_s2,
                   t->tmp.first, t->tmp.count, t->tmp.left, t->tmp.right, t->tmp.depth, t->tmp.M,
                   t->tmp.cx, t->tmp.cy, t->tmp.cz, t->tmp.s, t->cnt_start, t->min_depth,
                   t->start_off, t->scan_tmp, t->pf, t->ph, t->c.first, t->c.count, t->c.left,
@@ -762,7 +1170,9 @@ void free_build_buffers(kdfmm_tree_s* t) {
   t->segB = t->segL = nullptr;
   t->chunk_seg = t->seg_chunk_off = t->chunk_left = t->chunk_loff = t->seg_axis = t->seg_nl = nullptr;
   t->chunk_sum = t->seg_cut = nullptr;
-  t->chunk_key = t->chunk_s2 = nullptr;
+  t->chunk_key = nullptr;
+  t->chunk_s2 = t->seg_xb = t->seg_thr2 = nullptr;
+  t->seg_s2 = nullptr;
   t->tmp = TmpCells{};
   t->cnt_start = t->min_depth = t->start_off = t->scan_tmp = nullptr;
   t->pf = t->ph = nullptr;
@@ -805,6 +1215,9 @@ static int ensure_build_buffers(kdfmm_tree_s* t, int64_t n) {
   KD_ALLOC(t->seg_axis, t->capA);
   KD_ALLOC(t->seg_cut, t->capA);
   KD_ALLOC(t->seg_nl, t->capA);
+  KD_ALLOC(t->seg_xb, t->capA);
+  KD_ALLOC(t->seg_thr2, t->capA);
+  KD_ALLOC(t->seg_s2, t->capA);
   t->cap_cells = 2 * n + 2;
   const int64_t nc = t->cap_cells;
   KD_ALLOC(t->tmp.first, nc); KD_ALLOC(t->tmp.count, nc); KD_ALLOC(t->tmp.left, nc);
@@ -874,17 +1287,20 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
                                                   t->buf[src], t->chunk_sum, t->chunk_key);
     k_decide<<<blocks_for((int64_t)nA * 32, 256), 256, 0, s>>>(segs, nA, t->seg_chunk_off,
                                                                t->chunk_sum, t->chunk_key, t->tmp,
-                                                               t->seg_axis, t->seg_cut);
+                                                               t->seg_axis, t->seg_cut, t->seg_xb,
+                                                               t->seg_s2);
     k_chunk_count<<<maxc, kChunkThreads, 0, s>>>(segs, t->chunk_seg, t->seg_chunk_off, t->counters,
                                                  t->buf[src], t->tmp, t->seg_axis, t->seg_cut,
                                                  t->chunk_left, t->chunk_s2);
     k_split<<<blocks_for((int64_t)nA * 32, 256), 256, 0, s>>>(
-        segs, nA, t->seg_chunk_off, t->chunk_left, t->chunk_s2, t->chunk_loff, t->seg_nl, A, next,
-        t->segB, t->segL, dst);
+        segs, nA, t->seg_chunk_off, t->chunk_left, t->chunk_s2, t->chunk_loff, t->seg_nl, t->seg_xb,
+        t->seg_thr2, A, next, t->segB, t->segL, dst);
     k_chunk_scatter<<<maxc, kChunkThreads, 0, s>>>(segs, t->chunk_seg, t->seg_chunk_off, t->counters,
                                                    t->buf[src], t->buf[dst], t->seg_axis, t->seg_cut,
-                                                   t->chunk_loff, t->seg_nl);
-    t->launches += 6;
+                                                   t->chunk_loff, t->seg_nl, t->tmp, t->seg_thr2,
+                                                   t->seg_s2);
+    k_seg_size<<<blocks_for(nA, 128), 128, 0, s>>>(segs, nA, t->seg_s2, t->tmp);
+    t->launches += 7;
     rc = check_cuda(cudaMemcpyAsync(hc, t->counters, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
                     "counters");
     if (rc) return rc;
@@ -907,8 +1323,8 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
   S.segB = t->segB;
   S.qcap = kSubtreeMax / (P.n_leaf + 1) + 2;
   if (nB > 0) {
-    size_t smem = 4 * kSubtreeMax * sizeof(double) + 2 * kSubtreeMax * sizeof(uint16_t) +
-                  2 * (size_t)S.qcap * sizeof(int4);
+    size_t smem = 4 * kSubtreeMax * sizeof(double) + 3 * kSubtreeMax * sizeof(float) +
+                  2 * kSubtreeMax * sizeof(uint16_t) + 4 * (size_t)S.qcap * sizeof(int4);
     rc = check_cuda(cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem),
                     "subtree smem attribute");
@@ -917,7 +1333,7 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
     t->launches += 1;
   }
   if (nL > 0) {
-    k_leaf_segs<<<blocks_for((int64_t)nL * 32, 256), 256, 0, s>>>(S, t->segL, nL);
+    k_leaf_segs<<<blocks_for((int64_t)nL, 128), 128, 0, s>>>(S, t->segL, nL);
     t->launches += 1;
   }
   rc = check_cuda(cudaMemcpyAsync(hc, t->counters, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
@@ -941,20 +1357,21 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
   scan_i32(t->cnt_start, t->start_off, n, t->scan_tmp, s);
   k_remap<<<blocks_for(ncells, 256), 256, 0, s>>>(t->tmp, ncells, t->start_off, t->min_depth, t->c,
                                                   t->status);
-  cudaMemsetAsync(t->c.ready, 0, (size_t)ncells * sizeof(int32_t), s);
-  k_upward<<<blocks_for(ncells, 128), 128, 0, s>>>(t->c, ncells, t->tp);
-  // the arrival counters are free again: reuse them for the leaf flags
-  k_derive_cells<<<blocks_for(ncells, 256), 256, 0, s>>>(t->c, ncells, t->c.ready, t->com_bound);
+  k_leaf_flags<<<blocks_for(ncells, 256), 256, 0, s>>>(t->c, ncells, t->c.ready);
   scan_i32(t->c.ready, t->leaf_rank, ncells, t->scan_tmp, s);
   cudaMemcpyAsync(&t->host_counters[17], t->leaf_rank + ncells, sizeof(int32_t),
                   cudaMemcpyDeviceToHost, s);
   k_leaf_list<<<blocks_for(ncells, 256), 256, 0, s>>>(t->c, ncells, t->leaf_rank, t->leaf_cells);
-  t->launches += 12;
   cudaMemcpyAsync(&t->host_counters[16], t->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   if ((rc = check_cuda(cudaStreamSynchronize(s), "build finalise"))) return rc;
   t->nleaves = t->host_counters[17];
   if (t->host_counters[16] & ST_INTERNAL)
     return set_error(KDFMM_ERR_INTERNAL, "pre-order numbering inconsistent");
+  cudaMemsetAsync(t->c.ready, 0, (size_t)ncells * sizeof(int32_t), s);
+  k_upward<<<blocks_for((int64_t)t->nleaves, 128), 128, 0, s>>>(t->c, t->leaf_cells,
+                                                                     t->nleaves, t->tp);
+  k_derive_cells<<<blocks_for(ncells, 256), 256, 0, s>>>(t->c, ncells, t->com_bound);
+  t->launches += 13;
   k_particles32<<<blocks_for((int64_t)t->nleaves * 32, 256), 256, 0, s>>>(
       t->c, t->leaf_cells, t->nleaves, t->tp, t->pf, t->ph);
   t->launches += 1;

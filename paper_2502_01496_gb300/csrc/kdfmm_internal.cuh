@@ -59,12 +59,15 @@ struct Cells {
   int32_t* ready;            // bottom-up arrival counters
 };
 
+// Interaction lists: leaf k's far (M2L) list is far_idx[k * cap_far ...] with
+// far_cnt[k] entries, its near (P2P) list likewise; entries in ascending id.
 struct Lists {
   int32_t *far_cnt, *near_cnt;
-  int64_t *far_off, *near_off;     // nleaves + 1
+  int64_t *far_off, *near_off;     // nleaves + 1, filled only for export
   int32_t *far_idx, *near_idx;
-  int64_t far_cap, near_cap;
-  int64_t* near_np;                // per leaf: sum of near-leaf sizes
+  int64_t far_cap, near_cap;       // allocated entries
+  int64_t cap_far, cap_near;       // slot size per leaf
+  int64_t* near_np;                // device statistics of the walk (4)
 };
 
 }  // namespace kdfmm
@@ -90,7 +93,10 @@ struct kdfmm_tree_s {
   long long* chunk_key = nullptr;  // 6 per chunk: min xyz, max xyz
   int32_t* chunk_left = nullptr;
   int32_t* chunk_loff = nullptr;
-  long long* chunk_s2 = nullptr;
+  float* chunk_s2 = nullptr;         // per chunk: largest float32 squared distance
+  float* seg_xb = nullptr;           // per segment: bound on |coordinates|
+  float* seg_thr2 = nullptr;         // per segment: candidate threshold for the exact size
+  long long* seg_s2 = nullptr;       // per segment: exact squared size (as int64 bits)
   int32_t* seg_axis = nullptr;
   double* seg_cut = nullptr;
   int32_t* seg_nl = nullptr;
@@ -128,13 +134,39 @@ namespace kdfmm {
 // Device helpers
 // ---------------------------------------------------------------------------
 
-// Order-preserving int64 key of a double (for min / max with integer ops).
+// Order-preserving int64 key of a double (min / max / < with integer ops):
+// for non-NaN a, b: a < b exactly when dkey(a) < dkey(b) (-0 is keyed as +0).
 __device__ __forceinline__ long long dkey(double v) {
   long long b = __double_as_longlong(v);
+  if (b == (long long)0x8000000000000000ULL) b = 0;
   return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
 __device__ __forceinline__ double dunkey(long long k) {
   return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
+// float32 value of a double by truncating the mantissa, with integer
+// operations only: |result| <= |v| and |v - result| < 2^-23 |v| for normal
+// results; magnitudes below 2^-126 become zero, above the float range infinity.
+// Used where a float32 estimate with a known error bound is enough.
+__device__ __forceinline__ float trunc_to_float(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float(sign | ((unsigned)e << 23) | mant);
+}
+
+// Bound on |d_float32 - d| for a distance d whose coordinates and centre lie
+// within X of the origin, the coordinates taken as float32 by rounding or by
+// trunc_to_float (per component 2 x 2^-23 X, the difference, squares, sum and
+// square root), with a safety factor of more than 2.
+__device__ __forceinline__ float dist_err_bound(float X, float d) {
+  const float u = 5.9604645e-8f;
+  return 16.0f * u * (X + d) + 1e-37f;
 }
 
 struct Sum4 {

@@ -30,8 +30,9 @@ struct P2PArgs {
   const int32_t* leaf_cells;
   int nleaves;
   const int32_t *cfirst, *ccount;
-  const int64_t* near_off;
+  const int32_t* near_cnt;
   const int32_t* near_idx;
+  int64_t cap_near;
   const float4* src32;       // cell (hi, M), (lo, 0), ...
   const float4* pf;          // (x - com_leaf, m)
   const float4* ph;          // (1/h, 1/h^3, h, 0)
@@ -40,6 +41,8 @@ struct P2PArgs {
   const double *cy, *cz;
   const float* lexp32;
   const double* lexp64;
+  const float4* walk;        // cell (com, s) float32
+  const float2* walk2;       // cell (h_max, skip)
   float eps2f;
   double eps2;
   double* a;
@@ -100,6 +103,48 @@ __device__ __forceinline__ void pair32(float rx, float ry, float rz, float mj, c
     fx -= mf * rx; fy -= mf * ry; fz -= mf * rz;
     fp -= mj * p;
   }
+}
+
+// One side of the symmetrised M4 pair, branch-free: returns g/r (force per
+// unit displacement and mass) and psi for smoothing length h (hinv = 1/h,
+// hinv3 = 1/h^3), at distance r (inv = 1/r, inv3 = 1/r^3).
+//   q < 1     : g/r = h^-3 (4/3 - 6/5 q^2 + 1/2 q^3),
+//               psi = h^-1 (7/5 - 2/3 q^2 + 3/10 q^4 - 1/10 q^5)
+//   1 <= q < 2: g/r = r^-3 (1 - t^4 (1 - 4/5 t + t^2/6)),  t = 2 - q
+//               psi = 1/r + h^-1 R(q), R = 8/5 - 4/3 q^2 + q^3 - 3/10 q^4 + q^5/30 - 16/15 q^-1
+//   q >= 2    : g/r = r^-3, psi = 1/r  (t clamped to 0, R switched off)
+// (the [1,2) force is the enclosed mass 1 - int_q^2 (2-u)^3 u^2 du written in t).
+__device__ __forceinline__ void m4_side(float r, float inv, float inv3, float hinv, float hinv3,
+                                        float h, float& f, float& p) {
+  const float q = r * hinv;
+  const float q2 = q * q;
+  const float t = fmaxf(2.0f - q, 0.0f);
+  const float t2 = t * t;
+  const float g = 1.0f + t * (-0.8f + 0.16666667f * t);
+  const float f_out = inv3 * (1.0f - t2 * t2 * g);
+  const float f_in = hinv3 * (1.3333334f + q2 * (-1.2f + 0.5f * q));
+  f = q < 1.0f ? f_in : f_out;
+  const float p_in = hinv * (1.4f + q2 * (-0.6666667f + q2 * (0.3f - 0.1f * q)));
+  const float R = 1.6f + q2 * (-1.3333334f + q * (1.0f + q * (-0.3f + 0.033333335f * q))) -
+                  1.0666667f * (inv * h);
+  const float p_out = inv + (q < 2.0f ? hinv * R : 0.0f);
+  p = q < 1.0f ? p_in : p_out;
+}
+
+// Symmetrised M4 pair (Eq. 13), branch-free; hi / hj = (1/h, 1/h^3, h, -).
+__device__ __forceinline__ void m4pair32(float rx, float ry, float rz, float mj, const float4& hi,
+                                         const float4& hj, float& fx, float& fy, float& fz,
+                                         float& fp) {
+  const float r2 = fmaxf(rx * rx + ry * ry + rz * rz, 1e-30f);
+  const float inv = rsqrtf(r2);
+  const float r = r2 * inv;
+  const float inv3 = inv * inv * inv;
+  float fa, pa, fb, pb;
+  m4_side(r, inv, inv3, hi.x, hi.y, hi.z, fa, pa);
+  m4_side(r, inv, inv3, hj.x, hj.y, hj.z, fb, pb);
+  const float mf = 0.5f * mj * (fa + fb);
+  fx -= mf * rx; fy -= mf * ry; fz -= mf * rz;
+  fp -= 0.5f * mj * (pa + pb);
 }
 
 template <int SOFT>
@@ -173,11 +218,37 @@ __device__ __forceinline__ void near_leaf32(const P2PArgs& A, int fb, int nb, in
   }
 }
 
+// Newtonian pair (no kernel softening, optional Plummer eps^2), float32.
+__device__ __forceinline__ void newton32(float rx, float ry, float rz, float mj, float eps2,
+                                         float& fx, float& fy, float& fz, float& fp) {
+  const float r2 = rx * rx + ry * ry + rz * rz + eps2;
+  const float inv = rsqrtf(r2);
+  const float minv = mj * inv;
+  const float f = minv * inv * inv;
+  fx -= f * rx; fy -= f * ry; fz -= f * rz;
+  fp -= minv;
+}
+
+constexpr int kStageCap = 256;     // staged sources per warp and chunk
+constexpr int kP2PWarps = 4;
+
+// Mixed precision.  Per chunk of near leaves the warp stages their particles
+// in shared memory, shifted to the target leaf's centre of mass, and splits
+// them into sources that lie outside the kernel support of every target
+// (|s| - s_alpha >= 2 max(h_max,alpha, h_j): plain 1/r^2, Eq. 15) and sources
+// that may not (full M4 pair).  The split only selects the instruction path:
+// the M4 pair reduces to the same 1/r^2 outside the support.  The target's
+// own leaf is summed separately so that j = i is skipped exactly.
 template <int SOFT>
-__global__ void __launch_bounds__(256) k_p2p_mixed(P2PArgs A) {
-  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
+  constexpr bool M4 = SOFT == KDFMM_SOFT_M4;
+  __shared__ float4 s_pos[kP2PWarps][kStageCap];
+  __shared__ float4 s_ker[M4 ? kP2PWarps : 1][M4 ? kStageCap : 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * kP2PWarps + warp;
   if (k >= A.nleaves) return;
+  float4* sp = s_pos[warp];
+  float4* sk = s_ker[M4 ? warp : 0];
   const int a = A.leaf_cells[k];
   const int fa = A.cfirst[a], nt = A.ccount[a];
   const int K = 32 / nt;
@@ -185,35 +256,106 @@ __global__ void __launch_bounds__(256) k_p2p_mixed(P2PArgs A) {
   const bool act = sl < K;
   const float4 xa = A.pf[fa + t];
   float4 hi = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (SOFT == KDFMM_SOFT_M4) hi = A.ph[fa + t];
+  if (M4) hi = A.ph[fa + t];
   const float4 ca = A.src32[4 * a], cal = A.src32[4 * a + 1];
+  const float sa = A.walk[a].w, hmax_a = A.walk2[a].x;
   float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, azh = 0.f, azl = 0.f, ph_ = 0.f, pl = 0.f;
-  const int64_t e0 = A.near_off[k], e1 = A.near_off[k + 1];
-  for (int64_t e = e0; e < e1; ++e) {
-    const int b = A.near_idx[e];
-    const int fb = A.cfirst[b], nb = A.ccount[b];
-    const float4 cb = A.src32[4 * b], cbl = A.src32[4 * b + 1];
-    // target relative to the source leaf's centre of mass
-    const float xs = xa.x - ((cb.x - ca.x) + (cbl.x - cal.x));
-    const float ys = xa.y - ((cb.y - ca.y) + (cbl.y - cal.y));
-    const float zs = xa.z - ((cb.z - ca.z) + (cbl.z - cal.z));
+  {
+    float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;
+    if (act) near_leaf32<SOFT, true>(A, fa, nt, sl, K, t, xa.x, xa.y, xa.z, hi, fx, fy, fz, fp);
+    df_add(axh, axl, fx); df_add(ayh, ayl, fy); df_add(azh, azl, fz); df_add(ph_, pl, fp);
+  }
+  const unsigned full = 0xffffffffu, lt = (1u << lane) - 1u;
+  const int64_t e1 = (int64_t)k * A.cap_near + A.near_cnt[k];
+  for (int64_t e = (int64_t)k * A.cap_near; e < e1;) {
+    // up to 32 candidate leaves, one per lane
+    const int64_t my = e + lane;
+    int cnt = 0, first = 0;
+    float dx = 0.f, dy = 0.f, dz = 0.f;
+    if (my < e1) {
+      const int b = A.near_idx[my];
+      if (b != a) {
+        cnt = A.ccount[b];
+        first = A.cfirst[b];
+        const float4 cb = A.src32[4 * b], cbl = A.src32[4 * b + 1];
+        dx = (cb.x - ca.x) + (cbl.x - cal.x);
+        dy = (cb.y - ca.y) + (cbl.y - cal.y);
+        dz = (cb.z - ca.z) + (cbl.z - cal.z);
+      }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int w = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += w;
+    }
+    const int L = __popc(__ballot_sync(full, my < e1 && incl <= kStageCap));
+    // stage the chunk's sources: two leaves per pass (half-warps), 16 particles each step
+    int nN = 0, nK = 0;
+    const int half = lane >> 4, hl = lane & 15;
+    for (int l = 0; l < L; l += 2) {
+      const int ll = min(l + half, 31);
+      int lc = __shfl_sync(full, cnt, ll);
+      if (l + half >= L) lc = 0;
+      const int lf = __shfl_sync(full, first, ll);
+      const float ldx = __shfl_sync(full, dx, ll), ldy = __shfl_sync(full, dy, ll),
+                  ldz = __shfl_sync(full, dz, ll);
+      const int cmax = max(__shfl_sync(full, lc, 0), __shfl_sync(full, lc, 16));
+      for (int j0 = 0; j0 < cmax; j0 += 16) {
+        const int j = j0 + hl;
+        const bool v = j < lc;
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f), hk = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool need = false;
+        if (v) {
+          p = A.pf[lf + j];
+          p.x += ldx; p.y += ldy; p.z += ldz;
+          if (M4) {
+            hk = A.ph[lf + j];
+            const float d = sqrtf(p.x * p.x + p.y * p.y + p.z * p.z);
+            need = d - sa < 2.0f * fmaxf(hmax_a, hk.z) * 1.0001f + 1e-20f;
+          }
+        }
+        const unsigned vm = __ballot_sync(full, v), nm = __ballot_sync(full, v && need);
+        if (v) {
+          if (need) {
+            const int pos = kStageCap - 1 - (nK + __popc(nm & lt));
+            sp[pos] = p;
+            sk[pos] = hk;
+          } else {
+            sp[nN + __popc(vm & ~nm & lt)] = p;
+          }
+        }
+        nK += __popc(nm);
+        nN += __popc(vm & ~nm);
+      }
+    }
+    __syncwarp();
     float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;
     if (act) {
-      if (b == a) near_leaf32<SOFT, true>(A, fb, nb, sl, K, t, xs, ys, zs, hi, fx, fy, fz, fp);
-      else near_leaf32<SOFT, false>(A, fb, nb, sl, K, t, xs, ys, zs, hi, fx, fy, fz, fp);
+#pragma unroll 4
+      for (int j = sl; j < nN; j += K) {
+        const float4 s = sp[j];
+        newton32(xa.x - s.x, xa.y - s.y, xa.z - s.z, s.w, A.eps2f, fx, fy, fz, fp);
+      }
+      if (M4) {
+#pragma unroll 1
+        for (int j = kStageCap - nK + sl; j < kStageCap; j += K) {
+          const float4 s = sp[j];
+          m4pair32(xa.x - s.x, xa.y - s.y, xa.z - s.z, s.w, hi, sk[j], fx, fy, fz, fp);
+        }
+      }
     }
-    df_add(axh, axl, fx);
-    df_add(ayh, ayl, fy);
-    df_add(azh, azl, fz);
-    df_add(ph_, pl, fp);
+    df_add(axh, axl, fx); df_add(ayh, ayl, fy); df_add(azh, azl, fz); df_add(ph_, pl, fp);
+    __syncwarp();
+    e += L;
   }
   // combine the source slices of each target
   for (int s = 1; s < K; ++s) {
     const int src = t + s * nt;
-    const float bxh = __shfl_sync(0xffffffffu, axh, src), bxl = __shfl_sync(0xffffffffu, axl, src);
-    const float byh = __shfl_sync(0xffffffffu, ayh, src), byl = __shfl_sync(0xffffffffu, ayl, src);
-    const float bzh = __shfl_sync(0xffffffffu, azh, src), bzl = __shfl_sync(0xffffffffu, azl, src);
-    const float bph = __shfl_sync(0xffffffffu, ph_, src), bpl = __shfl_sync(0xffffffffu, pl, src);
+    const float bxh = __shfl_sync(full, axh, src), bxl = __shfl_sync(full, axl, src);
+    const float byh = __shfl_sync(full, ayh, src), byl = __shfl_sync(full, ayl, src);
+    const float bzh = __shfl_sync(full, azh, src), bzl = __shfl_sync(full, azl, src);
+    const float bph = __shfl_sync(full, ph_, src), bpl = __shfl_sync(full, pl, src);
     if (sl == 0) {
       df_add2(axh, axl, bxh, bxl);
       df_add2(ayh, ayl, byh, byl);
@@ -248,7 +390,7 @@ __global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
   const int64_t it = (int64_t)fa + t;
   const double xi = A.tp.x[it], yi = A.tp.y[it], zi = A.tp.z[it], hi = A.tp.h[it];
   double fx = 0.0, fy = 0.0, fz = 0.0, fp = 0.0;
-  const int64_t e0 = A.near_off[k], e1 = A.near_off[k + 1];
+  const int64_t e0 = (int64_t)k * A.cap_near, e1 = e0 + A.near_cnt[k];
   if (act) {
     for (int64_t e = e0; e < e1; ++e) {
       const int b = A.near_idx[e];
@@ -289,7 +431,8 @@ int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s) {
   A.nleaves = t->nleaves;
   A.cfirst = t->c.first;
   A.ccount = t->c.count;
-  A.near_off = t->L.near_off;
+  A.near_cnt = t->L.near_cnt;
+  A.cap_near = t->L.cap_near;
   A.near_idx = t->L.near_idx;
   A.src32 = t->c.src32;
   A.pf = t->pf;
@@ -298,6 +441,8 @@ int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s) {
   A.cx = t->c.cx; A.cy = t->c.cy; A.cz = t->c.cz;
   A.lexp32 = t->lexp32;
   A.lexp64 = t->lexp64;
+  A.walk = t->c.walk;
+  A.walk2 = t->c.walk2;
   A.eps2 = t->p.eps * t->p.eps;
   A.eps2f = (float)A.eps2;
   A.a = a;
@@ -305,8 +450,9 @@ int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s) {
   const unsigned g = blocks_for((int64_t)t->nleaves * 32, 256);
   const bool m4 = t->p.soft_kind == KDFMM_SOFT_M4;
   if (t->p.precision == KDFMM_MIXED) {
-    if (m4) k_p2p_mixed<KDFMM_SOFT_M4><<<g, 256, 0, s>>>(A);
-    else k_p2p_mixed<KDFMM_SOFT_PLUMMER><<<g, 256, 0, s>>>(A);
+    const unsigned gm = blocks_for(t->nleaves, kP2PWarps);
+    if (m4) k_p2p_mixed<KDFMM_SOFT_M4><<<gm, kP2PWarps * 32, 0, s>>>(A);
+    else k_p2p_mixed<KDFMM_SOFT_PLUMMER><<<gm, kP2PWarps * 32, 0, s>>>(A);
   } else {
     if (m4) k_p2p_fp64<KDFMM_SOFT_M4><<<g, 256, 0, s>>>(A);
     else k_p2p_fp64<KDFMM_SOFT_PLUMMER><<<g, 256, 0, s>>>(A);

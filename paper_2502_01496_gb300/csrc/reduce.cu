@@ -148,17 +148,36 @@ __global__ void k_momentum_blocks(const double* __restrict__ m, const double* __
   if (threadIdx.x < 6) part[6 * blockIdx.x + threadIdx.x] = sh[0][threadIdx.x];
 }
 
+// Combines the partials: thread t folds partials t, t + 256, ... with two-sum,
+// then a fixed-order tree over the threads.  Deterministic for a given count.
 __global__ void k_momentum_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
-  if (threadIdx.x >= 3) return;
-  const int c = threadIdx.x;
-  double hi = 0.0, lo = 0.0;
-  for (int b = 0; b < nb; ++b) {
-    double s, e;
-    two_sum_d(hi, part[6 * b + 2 * c], s, e);
-    hi = s;
-    lo = __dadd_rn(__dadd_rn(lo, part[6 * b + 2 * c + 1]), e);
+  __shared__ double sh[kMomThreads][6];
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nb; b += kMomThreads) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double s, e;
+      two_sum_d(v[2 * c], part[6 * b + 2 * c], s, e);
+      v[2 * c] = s;
+      v[2 * c + 1] = __dadd_rn(__dadd_rn(v[2 * c + 1], part[6 * b + 2 * c + 1]), e);
+    }
   }
-  out[c] = __dadd_rn(hi, lo);
+  for (int j = 0; j < 6; ++j) sh[threadIdx.x][j] = v[j];
+  __syncthreads();
+  for (int stride = kMomThreads / 2; stride > 0; stride >>= 1) {
+    if (threadIdx.x < stride) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double s, e;
+        two_sum_d(sh[threadIdx.x][2 * c], sh[threadIdx.x + stride][2 * c], s, e);
+        sh[threadIdx.x][2 * c] = s;
+        sh[threadIdx.x][2 * c + 1] =
+            __dadd_rn(__dadd_rn(sh[threadIdx.x][2 * c + 1], sh[threadIdx.x + stride][2 * c + 1]), e);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) out[threadIdx.x] = __dadd_rn(sh[0][2 * threadIdx.x], sh[0][2 * threadIdx.x + 1]);
 }
 
 }  // namespace
@@ -185,7 +204,7 @@ int momentum(const double* m, const double* v, int64_t n, double* out, double* s
   int64_t nb = momentum_blocks(n);
   int64_t per = (n + nb - 1) / nb;
   k_momentum_blocks<<<(unsigned)nb, kMomThreads, 0, s>>>(m, v, n, per, scratch);
-  k_momentum_final<<<1, 32, 0, s>>>(scratch, (int)nb, out);
+  k_momentum_final<<<1, kMomThreads, 0, s>>>(scratch, (int)nb, out);
   return check_cuda(cudaGetLastError(), "momentum launch");
 }
 

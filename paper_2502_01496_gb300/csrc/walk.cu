@@ -15,6 +15,8 @@
 // mass, the sizes, theta and every operation); only a decision inside the
 // margin (about 1e-6 relative) is re-evaluated in float64 with the reference's
 // expression order and no contraction.
+#include <algorithm>
+
 #include "kdfmm_internal.cuh"
 
 namespace kdfmm {
@@ -31,9 +33,10 @@ struct WalkArgs {
   const float* com_bound;
   double theta, r_kern;
   int32_t *far_cnt, *near_cnt;
-  const int64_t *far_off, *near_off;
-  int32_t *far_idx, *near_idx;
-  unsigned long long* stats;   // [0] P2P interactions, [1] float64 decisions
+  int32_t *far_idx, *near_idx;     // leaf k's lists start at k * cap_far / k * cap_near
+  int64_t cap_far, cap_near;
+  int32_t* maxc;                   // [0] longest far list, [1] longest near list
+  unsigned long long* stats;       // [0] P2P interactions, [1] float64 decisions, [2] far, [3] near
 };
 
 __device__ __forceinline__ bool open_exact(double ax, double ay, double az, double sa, double ha,
@@ -65,7 +68,9 @@ __device__ __forceinline__ int open_filter(float4 a, float ha, float4 b, float h
   return -1;
 }
 
-template <bool FILL>
+// One thread per leaf, one pass: the lists go to fixed-capacity slots of the
+// leaf (entries beyond the capacity are counted, not stored; the host then
+// grows the slots and walks again).
 __global__ void __launch_bounds__(128) k_walk(WalkArgs W) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= W.nleaves) return;
@@ -76,8 +81,8 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs W) {
   const float bound = *W.com_bound;
   const float thf = (float)W.theta, rkf = (float)W.r_kern;
   const bool always = W.theta == 0.0;
-  int64_t fo = 0, no = 0;
-  if (FILL) { fo = W.far_off[k]; no = W.near_off[k]; }
+  int32_t* far = W.far_idx + (int64_t)k * W.cap_far;
+  int32_t* near = W.near_idx + (int64_t)k * W.cap_near;
   int nf = 0, nn = 0, nex = 0;
   long long np = 0;
   int i = 0;
@@ -93,88 +98,102 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs W) {
     }
     if (o) {
       if (skip == i + 1) {                    // opened leaf: short range
-        if (FILL) W.near_idx[no + nn] = i;
-        else np += W.count[i];
+        if (nn < W.cap_near) near[nn] = i;
+        np += W.count[i];
         ++nn;
       }
       i = i + 1;
     } else {                                  // closed: long range, skip its subtree
-      if (FILL) W.far_idx[fo + nf] = i;
+      if (nf < W.cap_far) far[nf] = i;
       ++nf;
       i = skip;
     }
   }
-  if (!FILL) {
-    W.far_cnt[k] = nf;
-    W.near_cnt[k] = nn;
-    const long long na = W.count[a];
-    atomicAdd(&W.stats[0], (unsigned long long)(na * np - na));
-    if (nex) atomicAdd(&W.stats[1], (unsigned long long)nex);
-  }
+  W.far_cnt[k] = nf;
+  W.near_cnt[k] = nn;
+  atomicMax(&W.maxc[0], nf);
+  atomicMax(&W.maxc[1], nn);
+  const long long na = W.count[a];
+  atomicAdd(&W.stats[0], (unsigned long long)(na * np - na));
+  atomicAdd(&W.stats[2], (unsigned long long)nf);
+  atomicAdd(&W.stats[3], (unsigned long long)nn);
+  if (nex) atomicAdd(&W.stats[1], (unsigned long long)nex);
 }
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
 
-int ensure_lists(kdfmm_tree_s* t, int64_t nfar, int64_t nnear) {
+int ensure_lists(kdfmm_tree_s* t, int64_t cap_far, int64_t cap_near) {
   Lists& L = t->L;
-  if (L.far_cap < nfar) {
+  const int64_t nl = t->nleaves;
+  if (L.far_cap < nl * cap_far) {
     cudaFree(L.far_idx);
     L.far_idx = nullptr;
-    int64_t cap = nfar + nfar / 4 + 1024;
-    if (cudaMalloc(&L.far_idx, cap * sizeof(int32_t)) != cudaSuccess)
-      return set_error(KDFMM_ERR_OOM, "far list allocation (%lld entries)", (long long)cap);
-    L.far_cap = cap;
+    L.far_cap = 0;
+    if (cudaMalloc(&L.far_idx, nl * cap_far * sizeof(int32_t)) != cudaSuccess)
+      return set_error(KDFMM_ERR_OOM, "far list slots (%lld x %lld)", (long long)nl,
+                       (long long)cap_far);
+    L.far_cap = nl * cap_far;
   }
-  if (L.near_cap < nnear) {
+  if (L.near_cap < nl * cap_near) {
     cudaFree(L.near_idx);
     L.near_idx = nullptr;
-    int64_t cap = nnear + nnear / 4 + 1024;
-    if (cudaMalloc(&L.near_idx, cap * sizeof(int32_t)) != cudaSuccess)
-      return set_error(KDFMM_ERR_OOM, "near list allocation (%lld entries)", (long long)cap);
-    L.near_cap = cap;
+    L.near_cap = 0;
+    if (cudaMalloc(&L.near_idx, nl * cap_near * sizeof(int32_t)) != cudaSuccess)
+      return set_error(KDFMM_ERR_OOM, "near list slots (%lld x %lld)", (long long)nl,
+                       (long long)cap_near);
+    L.near_cap = nl * cap_near;
   }
+  L.cap_far = cap_far;
+  L.cap_near = cap_near;
   return KDFMM_OK;
 }
 
 int run_walk(kdfmm_tree_s* t, cudaStream_t s) {
   const int nl = t->nleaves;
-  WalkArgs W{};
-  W.walk = t->c.walk;
-  W.walk2 = t->c.walk2;
-  W.cx = t->c.cx; W.cy = t->c.cy; W.cz = t->c.cz; W.s = t->c.s; W.hmax = t->c.hmax;
-  W.count = t->c.count;
-  W.leaf_cells = t->leaf_cells;
-  W.nleaves = nl;
-  W.ncells = t->ncells;
-  W.com_bound = t->com_bound;
-  W.theta = t->p.theta;
-  W.r_kern = t->p.r_kern;
-  W.far_cnt = t->L.far_cnt;
-  W.near_cnt = t->L.near_cnt;
-  W.far_off = t->L.far_off;
-  W.near_off = t->L.near_off;
-  W.stats = reinterpret_cast<unsigned long long*>(t->L.near_np);
-  cudaMemsetAsync(t->L.near_np, 0, 4 * sizeof(int64_t), s);
-  k_walk<false><<<blocks_for(nl, 128), 128, 0, s>>>(W);
-  int64_t* tmp64 = reinterpret_cast<int64_t*>(t->scan_tmp);
-  scan_i32_to_i64(t->L.far_cnt, t->L.far_off, nl, tmp64, s);
-  scan_i32_to_i64(t->L.near_cnt, t->L.near_off, nl, tmp64, s);
-  int64_t* hs = t->host_stats;
-  cudaMemcpyAsync(hs + 16, t->L.far_off + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(hs + 17, t->L.near_off + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-  int rc = check_cuda(cudaStreamSynchronize(s), "walk count");
-  if (rc) return rc;
-  const int64_t nfar = hs[16], nnear = hs[17];
-  if ((rc = ensure_lists(t, nfar, nnear))) return rc;
-  W.far_idx = t->L.far_idx;
-  W.near_idx = t->L.near_idx;
-  k_walk<true><<<blocks_for(nl, 128), 128, 0, s>>>(W);
-  t->launches += 8;
-  t->host_stats[KDFMM_STAT_NFAR] = nfar;
-  t->host_stats[KDFMM_STAT_NNEAR] = nnear;
-  return check_cuda(cudaGetLastError(), "walk launch");
+  Lists& L = t->L;
+  int64_t cf = L.cap_far > 0 ? L.cap_far : 512, cn = L.cap_near > 0 ? L.cap_near : 128;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    int rc = ensure_lists(t, cf, cn);
+    if (rc) return rc;
+    WalkArgs W{};
+    W.walk = t->c.walk;
+    W.walk2 = t->c.walk2;
+    W.cx = t->c.cx; W.cy = t->c.cy; W.cz = t->c.cz; W.s = t->c.s; W.hmax = t->c.hmax;
+    W.count = t->c.count;
+    W.leaf_cells = t->leaf_cells;
+    W.nleaves = nl;
+    W.ncells = t->ncells;
+    W.com_bound = t->com_bound;
+    W.theta = t->p.theta;
+    W.r_kern = t->p.r_kern;
+    W.far_cnt = L.far_cnt;
+    W.near_cnt = L.near_cnt;
+    W.far_idx = L.far_idx;
+    W.near_idx = L.near_idx;
+    W.cap_far = cf;
+    W.cap_near = cn;
+    W.maxc = t->counters + 8;
+    W.stats = reinterpret_cast<unsigned long long*>(L.near_np);
+    cudaMemsetAsync(L.near_np, 0, 4 * sizeof(int64_t), s);
+    cudaMemsetAsync(t->counters + 8, 0, 2 * sizeof(int32_t), s);
+    k_walk<<<blocks_for(nl, 128), 128, 0, s>>>(W);
+    t->launches += 1;
+    int32_t* hc = t->host_counters;
+    cudaMemcpyAsync(hc + 8, t->counters + 8, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(t->host_stats + 16, L.near_np, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if ((rc = check_cuda(cudaStreamSynchronize(s), "walk"))) return rc;
+    const int64_t mf = hc[8], mn = hc[9];
+    if (mf <= cf && mn <= cn) {
+      t->host_stats[KDFMM_STAT_NFAR] = t->host_stats[16 + 2];
+      t->host_stats[KDFMM_STAT_NNEAR] = t->host_stats[16 + 3];
+      return check_cuda(cudaGetLastError(), "walk launch");
+    }
+    cf = std::max<int64_t>(cf, mf + mf / 4 + 16);
+    cn = std::max<int64_t>(cn, mn + mn / 4 + 16);
+  }
+  return set_error(KDFMM_ERR_CAPACITY, "interaction lists kept outgrowing their slots");
 }
 
 }  // namespace kdfmm
