@@ -108,10 +108,17 @@ void kdfmm_tree_destroy(kdfmm_tree t);
 int kdfmm_tree_build(kdfmm_tree t, const double* x, const double* m, const double* h, int64_t n,
                      const kdfmm_params* p, void* stream);
 
-/* Recomputes the cell moments (M, centre of mass, s, h_max, Q) of the existing
- * topology for new positions/masses/smoothing lengths of the same particles
- * (same caller order, same n).  Used to evaluate the force with the tree frozen.
- * Sums run in pairwise order over each cell's particles in tree order. */
+/* Moments for a frozen tree (Sec. 2; Eq. 7): recomputes M, centre of mass, s,
+ * h_max and Q of the existing cells for new positions / masses / smoothing
+ * lengths of the same particles (same caller order and n), and freezes the
+ * interaction lists of the last kdfmm_fmm_accel: later evaluations reuse them
+ * until the next kdfmm_tree_build.  This is the evaluation that
+ * kdfmm_fmm_accel_vjp differentiates (topology and lists held fixed), so finite
+ * differences of it check the adjoint.  Leaf sums are pairwise over the leaf's
+ * particles; a parent's M and sum m x are its left plus its right child's; s is
+ * the exact maximum distance; Q the parallel-axis shift of its children's.
+ * Needs one evaluation after the build.  Synchronises `stream`.
+ * Errors as kdfmm_tree_build. */
 int kdfmm_tree_moments(kdfmm_tree t, const double* x, const double* m, const double* h,
                        void* stream);
 
@@ -124,9 +131,19 @@ int kdfmm_fmm_accel(kdfmm_tree t, double* a, double* phi, void* stream);
 
 /* Vector-Jacobian product of the last evaluation's accelerations with respect
  * to positions and masses, through the same tree and interaction lists (the
- * lists and cell topology are held fixed).  a_bar: N x 3 cotangent; x_bar:
- * N x 3 and m_bar: N outputs (overwritten).  The paper has no adjoint; this is
- * the derivative of the evaluation that kdfmm_fmm_accel performs. */
+ * lists and cell topology are held fixed; smoothing lengths are inputs).
+ * The paper has no adjoint; this is the derivative of the evaluation that
+ * kdfmm_fmm_accel performs (Eqs. 3, 6, 7, 8, 13): L2P, M2L (r-derivatives by
+ * dual numbers, M and Q linear), P2P on the target and on the source side,
+ * and the moments (com = sum m x / M, Q of Eq. 7) back to the particles.
+ * a_bar: N x 3 cotangent (caller order, device); x_bar: N x 3 and m_bar: N
+ * outputs (device, overwritten).  Arithmetic is float64 in both precision
+ * modes (mixed mode uses the evaluation's float32 expansions); cell
+ * cotangents are summed with float64 atomics, so the last bits may vary run
+ * to run.  Allocates its scratch (about 56 bytes per particle plus the
+ * transposed near lists) with cudaMallocAsync on `stream`.  Errors:
+ * KDFMM_ERR_INVALID_ARG before any evaluation or for non-device pointers,
+ * KDFMM_ERR_CUDA on allocation or launch failure. */
 int kdfmm_fmm_accel_vjp(kdfmm_tree t, const double* a_bar, double* x_bar, double* m_bar,
                         void* stream);
 

@@ -66,6 +66,10 @@ def _load():
     L.orc_lists_free.argtypes = [P]
     L.orc_eval.restype = i32
     L.orc_eval.argtypes = [P, i32, P, P, P, P, P, P, P, P]
+    L.orc_eval_lists.restype = i32
+    L.orc_eval_lists.argtypes = [P, i32, P, P, P, P, P, P, P]
+    L.orc_moments_frozen.restype = i32
+    L.orc_moments_frozen.argtypes = [P, P, P, P]
     L.orc_direct.argtypes = [i64, P, P, P, i32, f64, i64, P, P, P]
     L.orc_monomials.restype = i32
     L.orc_monomials.argtypes = [P]
@@ -215,6 +219,31 @@ class Tree:
         if parts:
             return a, phi, dict(a_short=extra[0], a_long=extra[1], phi_short=extra[2],
                                 phi_long=extra[3], n_p2p=int(stats[0]), n_m2l=int(stats[1]))
+        return a, phi
+
+
+    def moments_frozen(self, x, m, h=None):
+        """New positions / masses / smoothing lengths for the same particles,
+        cells kept (frozen topology); see orc_moments_frozen."""
+        x, m = _f64(x, (-1, 3)), _f64(m)
+        h = None if h is None else _f64(h)
+        assert x.shape[0] == self.n
+        self.x, self.m, self.h = x, m, h
+        _load().orc_moments_frozen(self._t, _p(x), _p(m), _p(h))
+
+    def eval_lists(self, lists: "Lists"):
+        """a, phi (caller order) of every leaf from the given interaction lists."""
+        a = np.full((self.n, 3), np.nan)
+        phi = np.full(self.n, np.nan)
+        li = np.ascontiguousarray(lists.leaf_ids, dtype=np.int32)
+        fo = np.ascontiguousarray(lists.far_off, dtype=np.int64)
+        no = np.ascontiguousarray(lists.near_off, dtype=np.int64)
+        fi = np.ascontiguousarray(lists.far_idx, dtype=np.int32)
+        ni = np.ascontiguousarray(lists.near_idx, dtype=np.int32)
+        rc = _load().orc_eval_lists(self._t, len(li), _p(li), _p(fo), _p(fi), _p(no), _p(ni),
+                                    _p(a), _p(phi))
+        if rc != 0:
+            raise ValueError(f"oracle eval_lists failed ({rc})")
         return a, phi
 
 

@@ -569,9 +569,57 @@ void orc_lists_free(olists* L) {
 /* Force evaluation.                                                          */
 /* ------------------------------------------------------------------------ */
 
+/* Forces on the particles of leaf alpha from the given far and near lists:
+ * M2L of every far cell (Eq. 6) summed into one local expansion, L2P at each
+ * particle (Eq. 8), softened pair sums over the near leaves (j != i), and
+ * a = a_short + a_long (Eq. 3). */
+static void eval_leaf(const otree* T, int32_t alpha, const int32_t* far, int64_t nfar,
+                      const int32_t* near, int64_t nnear, double* a, double* phi, double* a_short,
+                      double* a_long, double* phi_short, double* phi_long, int64_t* npp) {
+    const ocell* ca = &T->cells[alpha];
+    local_exp L;
+    memset(&L, 0, sizeof L);
+    for (int64_t f = 0; f < nfar; ++f) {
+        const ocell* cb = &T->cells[far[f]];
+        double r[3] = {ca->com[0] - cb->com[0], ca->com[1] - cb->com[1], ca->com[2] - cb->com[2]};
+        local_add_m2l(&L, r, cb->M, cb->Q);
+    }
+    for (int64_t k = 0; k < ca->count; ++k) {
+        int64_t i = T->order[ca->first + k];
+        const double* xi = &T->x[3 * i];
+        double as[3] = {0, 0, 0}, ps = 0.0;
+        for (int64_t nb = 0; nb < nnear; ++nb) {
+            const ocell* cb = &T->cells[near[nb]];
+            for (int64_t q = 0; q < cb->count; ++q) {
+                int64_t j = T->order[cb->first + q];
+                if (j == i) continue;
+                const double* xj = &T->x[3 * j];
+                double d[3] = {xi[0] - xj[0], xi[1] - xj[1], xi[2] - xj[2]};
+                double aij[3], pij;
+                pair_interaction(d, T->m[j], T->h[i], T->h[j], T->soft_kind, T->eps, aij, &pij);
+                as[0] += aij[0]; as[1] += aij[1]; as[2] += aij[2];
+                ps += pij;
+                ++*npp;
+            }
+        }
+        double xrel[3] = {xi[0] - ca->com[0], xi[1] - ca->com[1], xi[2] - ca->com[2]};
+        double al[3], pl;
+        local_eval(&L, xrel, al, &pl);
+        for (int d = 0; d < 3; ++d) {
+            if (a) a[3 * i + d] = as[d] + al[d];                 /* Eq. 3 */
+            if (a_short) a_short[3 * i + d] = as[d];
+            if (a_long) a_long[3 * i + d] = al[d];
+        }
+        if (phi) phi[i] = ps + pl;
+        if (phi_short) phi_short[i] = ps;
+        if (phi_long) phi_long[i] = pl;
+    }
+}
+
 /* Evaluates a and phi (caller order) for the particles of the selected leaves
- * (all leaves when nsel < 0).  a_short / a_long / phi_short / phi_long may be
- * NULL.  Counts of P2P interactions and M2L pairs go to stats[0], stats[1]. */
+ * (all leaves when nsel < 0), walking the tree for each.  a_short / a_long /
+ * phi_short / phi_long may be NULL.  Counts of P2P interactions and M2L pairs
+ * go to stats[0], stats[1]. */
 int32_t orc_eval(const otree* T, int32_t nsel, const int32_t* sel, double* a, double* phi,
                  double* a_short, double* a_long, double* phi_short, double* phi_long,
                  int64_t* stats) {
@@ -581,55 +629,100 @@ int32_t orc_eval(const otree* T, int32_t nsel, const int32_t* sel, double* a, do
     for (int32_t t = 0; t < nl; ++t) {
         int32_t alpha = nsel < 0 ? t : sel[t];
         if (alpha < 0 || alpha >= T->ncells) return -1;
-        const ocell* ca = &T->cells[alpha];
-        if (ca->left >= 0) {
+        if (T->cells[alpha].left >= 0) {
             if (nsel < 0) continue;
             return -2;
         }
         ivec far = {0}, near = {0};
         walk_rec(T, alpha, 0, &far, &near);
-        local_exp L;
-        memset(&L, 0, sizeof L);
-        for (int64_t f = 0; f < far.n; ++f) {
-            const ocell* cb = &T->cells[far.v[f]];
-            double r[3] = {ca->com[0] - cb->com[0], ca->com[1] - cb->com[1], ca->com[2] - cb->com[2]};
-            local_add_m2l(&L, r, cb->M, cb->Q);
-        }
+        eval_leaf(T, alpha, far.v, far.n, near.v, near.n, a, phi, a_short, a_long, phi_short,
+                  phi_long, &npp);
         nm2l += far.n;
-        for (int64_t k = 0; k < ca->count; ++k) {
-            int64_t i = T->order[ca->first + k];
-            const double* xi = &T->x[3 * i];
-            double as[3] = {0, 0, 0}, ps = 0.0;
-            for (int64_t nb = 0; nb < near.n; ++nb) {
-                const ocell* cb = &T->cells[near.v[nb]];
-                for (int64_t q = 0; q < cb->count; ++q) {
-                    int64_t j = T->order[cb->first + q];
-                    if (j == i) continue;
-                    const double* xj = &T->x[3 * j];
-                    double d[3] = {xi[0] - xj[0], xi[1] - xj[1], xi[2] - xj[2]};
-                    double aij[3], pij;
-                    pair_interaction(d, T->m[j], T->h[i], T->h[j], T->soft_kind, T->eps, aij, &pij);
-                    as[0] += aij[0]; as[1] += aij[1]; as[2] += aij[2];
-                    ps += pij;
-                    ++npp;
-                }
-            }
-            double xrel[3] = {xi[0] - ca->com[0], xi[1] - ca->com[1], xi[2] - ca->com[2]};
-            double al[3], pl;
-            local_eval(&L, xrel, al, &pl);
-            for (int d = 0; d < 3; ++d) {
-                if (a) a[3 * i + d] = as[d] + al[d];                 /* Eq. 3 */
-                if (a_short) a_short[3 * i + d] = as[d];
-                if (a_long) a_long[3 * i + d] = al[d];
-            }
-            if (phi) phi[i] = ps + pl;
-            if (phi_short) phi_short[i] = ps;
-            if (phi_long) phi_long[i] = pl;
-        }
         free(far.v);
         free(near.v);
     }
     if (stats) { stats[0] = npp; stats[1] = nm2l; }
+    return 0;
+}
+
+/* Evaluation with given interaction lists (frozen topology): leaf_ids[k] is
+ * the k-th leaf, its lists far_idx[far_off[k] .. far_off[k+1]) and near_idx
+ * likewise.  All leaves are evaluated. */
+int32_t orc_eval_lists(const otree* T, int32_t nleaves, const int32_t* leaf_ids,
+                       const int64_t* far_off, const int32_t* far_idx, const int64_t* near_off,
+                       const int32_t* near_idx, double* a, double* phi) {
+    jet_init();
+    int64_t npp = 0;
+    for (int32_t k = 0; k < nleaves; ++k) {
+        int32_t alpha = leaf_ids[k];
+        if (alpha < 0 || alpha >= T->ncells || T->cells[alpha].left >= 0) return -1;
+        eval_leaf(T, alpha, far_idx + far_off[k], far_off[k + 1] - far_off[k], near_idx + near_off[k],
+                  near_off[k + 1] - near_off[k], a, phi, NULL, NULL, NULL, NULL, &npp);
+    }
+    return 0;
+}
+
+/* Frozen topology: new positions, masses and smoothing lengths for the same
+ * particles with the tree's cells kept.  A leaf's M and sum m x are pairwise
+ * sums over its particles (tree order); a super-cell's are its left child's
+ * plus its right child's; the centre of mass their ratio; s the exact maximum
+ * distance; Q by definition (Eq. 7); h_max the maximum.  Cells are visited in
+ * reverse pre-order, so children come before their parents. */
+int32_t orc_moments_frozen(otree* T, const double* x, const double* m, const double* h) {
+    memcpy(T->x, x, sizeof(double) * 3 * (size_t)T->n);
+    memcpy(T->m, m, sizeof(double) * (size_t)T->n);
+    for (int64_t i = 0; i < T->n; ++i)
+        T->h[i] = (T->soft_kind == SOFT_PLUMMER || h == NULL) ? T->eps : h[i];
+    double* S = (double*)malloc(sizeof(double) * 3 * (size_t)T->ncells);
+    T->vbuf = (double*)malloc(sizeof(double) * 4 * (size_t)T->n);
+    for (int32_t c = T->ncells - 1; c >= 0; --c) {
+        ocell* p = &T->cells[c];
+        if (p->left < 0) {
+            double* vm = T->vbuf;
+            double* vx = T->vbuf + p->count;
+            double* vy = T->vbuf + 2 * p->count;
+            double* vz = T->vbuf + 3 * p->count;
+            for (int64_t k = 0; k < p->count; ++k) {
+                int64_t i = T->order[p->first + k];
+                vm[k] = T->m[i];
+                vx[k] = T->m[i] * T->x[3 * i];
+                vy[k] = T->m[i] * T->x[3 * i + 1];
+                vz[k] = T->m[i] * T->x[3 * i + 2];
+            }
+            p->M = pairwise_sum(vm, p->count);
+            S[3 * c] = pairwise_sum(vx, p->count);
+            S[3 * c + 1] = pairwise_sum(vy, p->count);
+            S[3 * c + 2] = pairwise_sum(vz, p->count);
+        } else {
+            const ocell* l = &T->cells[p->left];
+            const ocell* r = &T->cells[p->right];
+            p->M = l->M + r->M;
+            for (int d = 0; d < 3; ++d) S[3 * c + d] = S[3 * p->left + d] + S[3 * p->right + d];
+        }
+        for (int d = 0; d < 3; ++d) p->com[d] = S[3 * c + d] / p->M;
+        double s2max = 0.0, hmax = 0.0, Q[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t k = 0; k < p->count; ++k) {
+            int64_t i = T->order[p->first + k];
+            double y0 = T->x[3 * i] - p->com[0], y1 = T->x[3 * i + 1] - p->com[1];
+            double y2 = T->x[3 * i + 2] - p->com[2];
+            double d2 = y0 * y0 + y1 * y1 + y2 * y2;
+            if (d2 > s2max) s2max = d2;
+            if (T->h[i] > hmax) hmax = T->h[i];
+            double mi = T->m[i];
+            Q[0] += mi * (3.0 * y0 * y0 - d2);
+            Q[1] += mi * (3.0 * y0 * y1);
+            Q[2] += mi * (3.0 * y0 * y2);
+            Q[3] += mi * (3.0 * y1 * y1 - d2);
+            Q[4] += mi * (3.0 * y1 * y2);
+            Q[5] += mi * (3.0 * y2 * y2 - d2);
+        }
+        p->s = sqrt(s2max);
+        p->hmax = hmax;
+        memcpy(p->Q, Q, sizeof Q);
+    }
+    free(S);
+    free(T->vbuf);
+    T->vbuf = NULL;
     return 0;
 }
 

@@ -153,7 +153,7 @@ int kdfmm_tree_build(kdfmm_tree t, const double* x, const double* m, const doubl
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev != t->device) return set_error(KDFMM_ERR_INVALID_ARG, "handle belongs to device %d", t->device);
-  t->built = t->evaluated = false;
+  t->built = t->evaluated = t->lists_frozen = false;
   t->n = n;
   t->p = *p;
   const int64_t old_cap = t->cap_n;
@@ -181,8 +181,12 @@ int kdfmm_tree_moments(kdfmm_tree t, const double* x, const double* m, const dou
     return set_error(KDFMM_ERR_INVALID_ARG, "x, m (and h) must be device pointers");
   if (t->p.soft_kind == KDFMM_SOFT_M4 && h == nullptr)
     return set_error(KDFMM_ERR_INVALID_ARG, "M4 kernel softening needs smoothing lengths h");
-  t->evaluated = false;
-  return recompute_moments(t, x, m, h, static_cast<cudaStream_t>(stream));
+  if (!t->evaluated && !t->lists_frozen)
+    return set_error(KDFMM_ERR_INVALID_ARG, "evaluate once (kdfmm_fmm_accel) before freezing the lists");
+  int rc = recompute_moments(t, x, m, h, static_cast<cudaStream_t>(stream));
+  if (rc) return rc;
+  t->lists_frozen = true;
+  return KDFMM_OK;
 }
 
 int kdfmm_fmm_accel(kdfmm_tree t, double* a, double* phi, void* stream) {
@@ -190,10 +194,12 @@ int kdfmm_fmm_accel(kdfmm_tree t, double* a, double* phi, void* stream) {
   if (!is_device_ptr(a) || (phi != nullptr && !is_device_ptr(phi)))
     return set_error(KDFMM_ERR_INVALID_ARG, "a (and phi) must be device pointers");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  phase_begin(t, KDFMM_PHASE_WALK, s);
-  int rc = run_walk(t, s);
-  if (rc) return rc;
-  phase_end(t, KDFMM_PHASE_WALK, s);
+  int rc = KDFMM_OK;
+  if (!t->lists_frozen) {              // after kdfmm_tree_moments the lists stay as they were
+    phase_begin(t, KDFMM_PHASE_WALK, s);
+    if ((rc = run_walk(t, s))) return rc;
+    phase_end(t, KDFMM_PHASE_WALK, s);
+  }
   phase_begin(t, KDFMM_PHASE_M2L, s);
   if ((rc = run_m2l(t, s))) return rc;
   phase_end(t, KDFMM_PHASE_M2L, s);
@@ -317,9 +323,10 @@ int kdfmm_tree_export(kdfmm_tree t, int64_t* perm, int64_t* cell_ints, double* c
 
 int kdfmm_fmm_accel_vjp(kdfmm_tree t, const double* a_bar, double* x_bar, double* m_bar,
                         void* stream) {
-  (void)a_bar; (void)x_bar; (void)m_bar; (void)stream;
   if (!t || !t->evaluated) return set_error(KDFMM_ERR_INVALID_ARG, "no evaluation to differentiate");
-  return set_error(KDFMM_ERR_INVALID_ARG, "adjoint not available in this build");
+  if (!is_device_ptr(a_bar) || !is_device_ptr(x_bar) || !is_device_ptr(m_bar))
+    return set_error(KDFMM_ERR_INVALID_ARG, "a_bar, x_bar and m_bar must be device pointers");
+  return run_vjp(t, a_bar, x_bar, m_bar, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

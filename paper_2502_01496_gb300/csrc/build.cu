@@ -1378,11 +1378,174 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
   return check_cuda(cudaGetLastError(), "build launch");
 }
 
-// Frozen-topology moments are not provided by this build.
+// ---------------------------------------------------------------------------
+// Frozen topology: new positions / masses / smoothing lengths for the same
+// particles, the tree's cells and the last interaction lists kept.  Leaf sums
+// are pairwise over the leaf's particles (tree order = ascending caller index
+// within a leaf); a parent's M and sum m x are its left child's plus its right
+// child's; s is the exact maximum distance; Q the parallel-axis shift.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_gather_frozen(const double* __restrict__ x, const double* __restrict__ m,
+                                const double* __restrict__ h, int64_t n, double eps, int soft_kind,
+                                PCols tp, int32_t* status) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int64_t i = tp.idx[p];
+  const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2], mi = m[i];
+  const double hi = (h != nullptr && soft_kind == KDFMM_SOFT_M4) ? h[i] : eps;
+  const bool ok = isfinite(xi) && isfinite(yi) && isfinite(zi) && isfinite(mi) && isfinite(hi) &&
+                  mi > 0.0 && (soft_kind == KDFMM_SOFT_M4 ? hi > 0.0 : hi >= 0.0);
+  if (!ok) atomicOr(status, ST_NONFINITE);
+  tp.x[p] = xi; tp.y[p] = yi; tp.z[p] = zi; tp.m[p] = mi; tp.h[p] = hi;
+}
+
+// Leaves: pairwise sums (carry stack), centre of mass, exact size, h_max, Q.
+__global__ void k_leaf_frozen(Cells c, const int32_t* __restrict__ leaf_cells, int nleaves, PCols tp,
+                              double* Sx, double* Sy, double* Sz) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nleaves) return;
+  const int t = leaf_cells[k];
+  const int f = c.first[t], cnt = c.count[t];
+  Sum4 st[8];
+  int top = 0;
+  for (int j = 0; j < cnt; ++j) {
+    const int64_t i = (int64_t)f + j;
+    Sum4 e = elem4(tp.m[i], tp.x[i], tp.y[i], tp.z[i]);
+    for (int kk = j; kk & 1; kk >>= 1) e = add4(st[--top], e);
+    st[top++] = e;
+  }
+  Sum4 v = st[top - 1];
+  for (int i = top - 2; i >= 0; --i) v = add4(st[i], v);
+  const double cx = __ddiv_rn(v.x, v.m), cy = __ddiv_rn(v.y, v.m), cz = __ddiv_rn(v.z, v.m);
+  long long s2 = 0;
+  double q[6] = {0, 0, 0, 0, 0, 0}, hm = 0.0;
+  for (int j = 0; j < cnt; ++j) {
+    const int64_t i = (int64_t)f + j;
+    s2 = max(s2, __double_as_longlong(dist2_rn(tp.x[i], tp.y[i], tp.z[i], cx, cy, cz)));
+    const double mi = tp.m[i];
+    const double y0 = tp.x[i] - cx, y1 = tp.y[i] - cy, y2 = tp.z[i] - cz;
+    const double y2s = y0 * y0 + y1 * y1 + y2 * y2;
+    q[0] += mi * (3.0 * y0 * y0 - y2s);
+    q[1] += mi * (3.0 * y0 * y1);
+    q[2] += mi * (3.0 * y0 * y2);
+    q[3] += mi * (3.0 * y1 * y1 - y2s);
+    q[4] += mi * (3.0 * y1 * y2);
+    q[5] += mi * (3.0 * y2 * y2 - y2s);
+    hm = fmax(hm, tp.h[i]);
+  }
+  c.M[t] = v.m; c.cx[t] = cx; c.cy[t] = cy; c.cz[t] = cz;
+  Sx[t] = v.x; Sy[t] = v.y; Sz[t] = v.z;
+  c.s[t] = sqrt(__longlong_as_double(s2));
+  c.hmax[t] = hm;
+  for (int j = 0; j < 6; ++j) c.Q[6 * t + j] = q[j];
+}
+
+// Parents from their children, bottom-up (the second child to finish goes on).
+__global__ void k_upward_frozen(Cells c, const int32_t* __restrict__ leaf_cells, int nleaves,
+                                double* Sx, double* Sy, double* Sz) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nleaves) return;
+  int cur = leaf_cells[k];
+  while (true) {
+    const int p = c.parent[cur];
+    if (p < 0) break;
+    __threadfence();
+    if (atomicAdd(&c.ready[p], 1) == 0) break;
+    __threadfence();
+    const int L = c.left[p], R = c.right[p];
+    const double M = __dadd_rn(__ldcg(&c.M[L]), __ldcg(&c.M[R]));
+    const double sx = __dadd_rn(__ldcg(&Sx[L]), __ldcg(&Sx[R]));
+    const double sy = __dadd_rn(__ldcg(&Sy[L]), __ldcg(&Sy[R]));
+    const double sz = __dadd_rn(__ldcg(&Sz[L]), __ldcg(&Sz[R]));
+    const double px = __ddiv_rn(sx, M), py = __ddiv_rn(sy, M), pz = __ddiv_rn(sz, M);
+    double q[6] = {0, 0, 0, 0, 0, 0}, hm = 0.0;
+    const int ch[2] = {L, R};
+    for (int side = 0; side < 2; ++side) {
+      const int kc = ch[side];
+      const double mk = __ldcg(&c.M[kc]);
+      const double d0 = __ldcg(&c.cx[kc]) - px, d1 = __ldcg(&c.cy[kc]) - py, d2 = __ldcg(&c.cz[kc]) - pz;
+      const double dd = d0 * d0 + d1 * d1 + d2 * d2;
+      q[0] += __ldcg(&c.Q[6 * kc + 0]) + mk * (3.0 * d0 * d0 - dd);
+      q[1] += __ldcg(&c.Q[6 * kc + 1]) + mk * (3.0 * d0 * d1);
+      q[2] += __ldcg(&c.Q[6 * kc + 2]) + mk * (3.0 * d0 * d2);
+      q[3] += __ldcg(&c.Q[6 * kc + 3]) + mk * (3.0 * d1 * d1 - dd);
+      q[4] += __ldcg(&c.Q[6 * kc + 4]) + mk * (3.0 * d1 * d2);
+      q[5] += __ldcg(&c.Q[6 * kc + 5]) + mk * (3.0 * d2 * d2 - dd);
+      hm = fmax(hm, __ldcg(&c.hmax[kc]));
+    }
+    c.M[p] = M; c.cx[p] = px; c.cy[p] = py; c.cz[p] = pz;
+    Sx[p] = sx; Sy[p] = sy; Sz[p] = sz;
+    for (int j = 0; j < 6; ++j) c.Q[6 * p + j] = q[j];
+    c.hmax[p] = hm;
+    cur = p;
+  }
+}
+
+// Exact size of every super-cell: one warp per cell, float32 filter over
+// truncated coordinates, float64 for the candidates.
+__global__ void k_size_frozen(Cells c, int ncells, PCols tp) {
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= ncells || c.left[t] < 0) return;
+  const int64_t f = c.first[t];
+  const int cnt = c.count[t];
+  const double cx = c.cx[t], cy = c.cy[t], cz = c.cz[t];
+  const float cxf = trunc_to_float(cx), cyf = trunc_to_float(cy), czf = trunc_to_float(cz);
+  float d2m = 0.0f, X = fmaxf(fabsf(cxf), fmaxf(fabsf(cyf), fabsf(czf)));
+  for (int j = lane; j < cnt; j += 32) {
+    const float dx = trunc_to_float(tp.x[f + j]) - cxf, dy = trunc_to_float(tp.y[f + j]) - cyf,
+                dz = trunc_to_float(tp.z[f + j]) - czf;
+    d2m = fmaxf(d2m, dx * dx + dy * dy + dz * dz);
+    X = fmaxf(X, fmaxf(fabsf(trunc_to_float(tp.x[f + j])),
+                       fmaxf(fabsf(trunc_to_float(tp.y[f + j])), fabsf(trunc_to_float(tp.z[f + j])))));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    d2m = fmaxf(d2m, __shfl_xor_sync(0xffffffffu, d2m, o));
+    X = fmaxf(X, __shfl_xor_sync(0xffffffffu, X, o));
+  }
+  const float Dm = sqrtf(d2m);
+  const float thr = Dm - 2.0f * dist_err_bound(X * 1.000001f, Dm);
+  const float thr2 = thr > 0.0f ? thr * thr * (1.0f - 1e-6f) : -1.0f;
+  long long s2 = 0;
+  for (int j = lane; j < cnt; j += 32) {
+    const double px = tp.x[f + j], py = tp.y[f + j], pz = tp.z[f + j];
+    const float dx = trunc_to_float(px) - cxf, dy = trunc_to_float(py) - cyf,
+                dz = trunc_to_float(pz) - czf;
+    if (dx * dx + dy * dy + dz * dz >= thr2)
+      s2 = max(s2, __double_as_longlong(dist2_rn(px, py, pz, cx, cy, cz)));
+  }
+  s2 = warp_max_ll(s2);
+  if (lane == 0) c.s[t] = sqrt(__longlong_as_double(s2));
+}
+
+}  // namespace
+
 int recompute_moments(kdfmm_tree_s* t, const double* x, const double* m, const double* h,
                       cudaStream_t s) {
-  (void)t; (void)x; (void)m; (void)h; (void)s;
-  return set_error(KDFMM_ERR_INVALID_ARG, "frozen-topology moments not available in this build");
+  const int64_t n = t->n;
+  const int ncells = t->ncells, nl = t->nleaves;
+  cudaMemsetAsync(t->status, 0, sizeof(int32_t), s);
+  cudaMemsetAsync(t->com_bound, 0, sizeof(float), s);
+  k_gather_frozen<<<blocks_for(n, 256), 256, 0, s>>>(x, m, h, n, t->p.eps, t->p.soft_kind, t->tp,
+                                                     t->status);
+  double *Sx = t->tmp.cx, *Sy = t->tmp.cy, *Sz = t->tmp.cz;     // free after the build
+  k_leaf_frozen<<<blocks_for(nl, 128), 128, 0, s>>>(t->c, t->leaf_cells, nl, t->tp, Sx, Sy, Sz);
+  cudaMemsetAsync(t->c.ready, 0, (size_t)ncells * sizeof(int32_t), s);
+  k_upward_frozen<<<blocks_for(nl, 128), 128, 0, s>>>(t->c, t->leaf_cells, nl, Sx, Sy, Sz);
+  k_size_frozen<<<blocks_for((int64_t)ncells * 32, 256), 256, 0, s>>>(t->c, ncells, t->tp);
+  k_derive_cells<<<blocks_for(ncells, 256), 256, 0, s>>>(t->c, ncells, t->com_bound);
+  k_particles32<<<blocks_for((int64_t)nl * 32, 256), 256, 0, s>>>(t->c, t->leaf_cells, nl, t->tp,
+                                                                  t->pf, t->ph);
+  t->launches += 6;
+  cudaMemcpyAsync(&t->host_counters[16], t->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  int rc = check_cuda(cudaStreamSynchronize(s), "frozen moments");
+  if (rc) return rc;
+  if (t->host_counters[16] & ST_NONFINITE)
+    return set_error(KDFMM_ERR_NONFINITE, "non-finite position or non-positive mass / h");
+  return check_cuda(cudaGetLastError(), "frozen moments launch");
 }
 
 }  // namespace kdfmm

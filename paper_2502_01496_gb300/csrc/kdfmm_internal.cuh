@@ -78,7 +78,7 @@ struct kdfmm_tree_s {
   int32_t ncells = 0, nleaves = 0, depth = 0, nfallback = 0;
   int64_t cap_cells = 0;
   kdfmm_params p{};
-  bool built = false, evaluated = false;
+  bool built = false, evaluated = false, lists_frozen = false;
 
   // build scratch
   kdfmm::PCols buf[2]{};
@@ -304,6 +304,7 @@ int recompute_moments(kdfmm_tree_s* t, const double* x, const double* m, const d
 int run_walk(kdfmm_tree_s* t, cudaStream_t s);
 int run_m2l(kdfmm_tree_s* t, cudaStream_t s);
 int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s);
+int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, cudaStream_t s);
 int momentum(const double* m, const double* v, int64_t n, double* out, double* scratch,
              cudaStream_t s);
 // exclusive scan of n int32 (out may alias in); returns the total in *total_dev

@@ -1,0 +1,595 @@
+// Vector-Jacobian product of one force evaluation with respect to positions
+// and masses, through the same tree and interaction lists (topology, lists
+// and smoothing lengths held fixed).  The paper has no adjoint; this is the
+// derivative of the evaluation of Sec. 2 (Eqs. 3, 6, 7, 8, 13), in float64.
+//
+// a_i = sum_{j in near(leaf i), j != i} m_j K(x_i - x_j)            (P2P)
+//     + L(C_alpha, x_i - com_alpha)                                (L2P, Eq. 8)
+// C_alpha = sum_{beta in far(alpha)} C(com_alpha - com_beta, M_beta, Q_beta)   (M2L, Eq. 6)
+// with M, com = S/M (S = sum m x) and Q (Eq. 7) functions of the particles.
+//
+// Reverse order: L2P (cotangents of each leaf's expansion and of x_i, com),
+// M2L (cotangents of r = com_alpha - com_beta, M_beta, Q_beta: C is linear in M
+// and Q, its r-derivatives come from dual numbers), P2P on the target side and
+// on the source side (transposed near lists), then the moments: per cell the
+// cotangents (M_bar, com_bar, Q_bar) give m_bar_i and x_bar_i as a quadratic
+// polynomial in x_i, summed over the leaf's chain of ancestors.
+#include <algorithm>
+
+#include "kdfmm_internal.cuh"
+
+namespace kdfmm {
+
+namespace {
+
+inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// ---------------------------------------------------------------------------
+// M2L coefficients (same closed forms as the forward) on a dual-number type
+// ---------------------------------------------------------------------------
+struct Dual3 {
+  double v, d[3];
+};
+__device__ __forceinline__ Dual3 dconst(double v) { return Dual3{v, {0.0, 0.0, 0.0}}; }
+__device__ __forceinline__ Dual3 operator+(const Dual3& a, const Dual3& b) {
+  return Dual3{a.v + b.v, {a.d[0] + b.d[0], a.d[1] + b.d[1], a.d[2] + b.d[2]}};
+}
+__device__ __forceinline__ Dual3 operator-(const Dual3& a, const Dual3& b) {
+  return Dual3{a.v - b.v, {a.d[0] - b.d[0], a.d[1] - b.d[1], a.d[2] - b.d[2]}};
+}
+__device__ __forceinline__ Dual3 operator-(const Dual3& a) {
+  return Dual3{-a.v, {-a.d[0], -a.d[1], -a.d[2]}};
+}
+__device__ __forceinline__ Dual3 operator*(const Dual3& a, const Dual3& b) {
+  return Dual3{a.v * b.v,
+               {a.d[0] * b.v + a.v * b.d[0], a.d[1] * b.v + a.v * b.d[1], a.d[2] * b.v + a.v * b.d[2]}};
+}
+__device__ __forceinline__ Dual3& operator+=(Dual3& a, const Dual3& b) { return a = a + b; }
+__device__ __forceinline__ Dual3 rsqrt_dual(const Dual3& a) {
+  const double r = 1.0 / sqrt(a.v);
+  const double dr = -0.5 * r / a.v;
+  return Dual3{r, {dr * a.d[0], dr * a.d[1], dr * a.d[2]}};
+}
+
+template <class T>
+__device__ __forceinline__ T tc(double v);
+template <>
+__device__ __forceinline__ double tc<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ Dual3 tc<Dual3>(double v) { return dconst(v); }
+
+__device__ __forceinline__ double rs(double v) { return 1.0 / sqrt(v); }
+__device__ __forceinline__ Dual3 rs(const Dual3& v) { return rsqrt_dual(v); }
+
+template <class T>
+__device__ __forceinline__ T c2e(int a, int b, const T R[3], const T u[3], const T Qm[3][3], T s1,
+                                 T s2, T t2, T t3) {
+  T v = s2 * R[a] * R[b] + t3 * (R[a] * u[b] + R[b] * u[a]) + t2 * Qm[a][b];
+  if (a == b) v += s1;
+  return v;
+}
+
+template <class T>
+__device__ __forceinline__ T c3e(int a, int b, int c, const T R[3], const T u[3], const T Qm[3][3],
+                                 T s2, T s3, T t3, T t4) {
+  T d = tc<T>(0.0), du = tc<T>(0.0);
+  if (a == b) { d += R[c]; du += u[c]; }
+  if (a == c) { d += R[b]; du += u[b]; }
+  if (b == c) { d += R[a]; du += u[a]; }
+  return s3 * R[a] * R[b] * R[c] + s2 * d +
+         t4 * (R[b] * R[c] * u[a] + R[a] * R[c] * u[b] + R[a] * R[b] * u[c]) +
+         t3 * (R[a] * Qm[b][c] + R[b] * Qm[a][c] + R[c] * Qm[a][b] + du);
+}
+
+// 20 compact coefficients C0, C1 (3), C2 (6), C3 (10) of the potential
+// Phi = -M/R - Q_jk R_j R_k / (2 R^5) and its derivatives (see m2l.cu).
+template <class T>
+__device__ void m2l_coeffs_t(const T R[3], double M, const double Q[6], T out[20]) {
+  const T Qm[3][3] = {{tc<T>(Q[0]), tc<T>(Q[1]), tc<T>(Q[2])},
+                      {tc<T>(Q[1]), tc<T>(Q[3]), tc<T>(Q[4])},
+                      {tc<T>(Q[2]), tc<T>(Q[4]), tc<T>(Q[5])}};
+  const T R2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+  const T g0 = rs(R2);
+  const T i2 = g0 * g0;
+  const T g1 = -(g0 * i2);
+  const T g2 = tc<T>(-3.0) * g1 * i2;
+  const T g3 = tc<T>(-5.0) * g2 * i2;
+  const T g4 = tc<T>(-7.0) * g3 * i2;
+  const T g5 = tc<T>(-9.0) * g4 * i2;
+  T u[3];
+  for (int i = 0; i < 3; ++i) u[i] = Qm[i][0] * R[0] + Qm[i][1] * R[1] + Qm[i][2] * R[2];
+  const T q = R[0] * u[0] + R[1] * u[1] + R[2] * u[2];
+  const T qs = q * tc<T>(1.0 / 6.0);
+  const T Mt = tc<T>(M);
+  const T s1 = -(Mt * g1) - g3 * qs;
+  const T s2 = -(Mt * g2) - g4 * qs;
+  const T s3 = -(Mt * g3) - g5 * qs;
+  const T t2 = g2 * tc<T>(-1.0 / 3.0), t3 = g3 * tc<T>(-1.0 / 3.0), t4 = g4 * tc<T>(-1.0 / 3.0);
+  out[0] = -(Mt * g0) - g2 * qs;
+  for (int i = 0; i < 3; ++i) out[1 + i] = s1 * R[i] + t2 * u[i];
+  out[4] = c2e<T>(0, 0, R, u, Qm, s1, s2, t2, t3);
+  out[5] = c2e<T>(0, 1, R, u, Qm, s1, s2, t2, t3);
+  out[6] = c2e<T>(0, 2, R, u, Qm, s1, s2, t2, t3);
+  out[7] = c2e<T>(1, 1, R, u, Qm, s1, s2, t2, t3);
+  out[8] = c2e<T>(1, 2, R, u, Qm, s1, s2, t2, t3);
+  out[9] = c2e<T>(2, 2, R, u, Qm, s1, s2, t2, t3);
+  out[10] = c3e<T>(0, 0, 0, R, u, Qm, s2, s3, t3, t4);
+  out[11] = c3e<T>(0, 0, 1, R, u, Qm, s2, s3, t3, t4);
+  out[12] = c3e<T>(0, 0, 2, R, u, Qm, s2, s3, t3, t4);
+  out[13] = c3e<T>(0, 1, 1, R, u, Qm, s2, s3, t3, t4);
+  out[14] = c3e<T>(0, 1, 2, R, u, Qm, s2, s3, t3, t4);
+  out[15] = c3e<T>(0, 2, 2, R, u, Qm, s2, s3, t3, t4);
+  out[16] = c3e<T>(1, 1, 1, R, u, Qm, s2, s3, t3, t4);
+  out[17] = c3e<T>(1, 1, 2, R, u, Qm, s2, s3, t3, t4);
+  out[18] = c3e<T>(1, 2, 2, R, u, Qm, s2, s3, t3, t4);
+  out[19] = c3e<T>(2, 2, 2, R, u, Qm, s2, s3, t3, t4);
+}
+
+// index of the compact C2 entry (a, b) and C3 entry (a, b, c)
+__device__ __forceinline__ int c2i(int a, int b) {
+  if (a > b) { int t = a; a = b; b = t; }
+  return a == 0 ? 4 + b : (a == 1 ? 6 + b : 9);
+}
+__device__ __forceinline__ int c3i(int a, int b, int c) {
+  // sort a <= b <= c
+  if (a > b) { int t = a; a = b; b = t; }
+  if (b > c) { int t = b; b = c; c = t; }
+  if (a > b) { int t = a; a = b; b = t; }
+  if (a == 0) return b == 0 ? 10 + c : (b == 1 ? 12 + c : 15);
+  if (a == 1) return b == 1 ? 15 + c : 18;
+  return 19;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+struct VjpArgs {
+  int64_t n;
+  int nleaves, ncells;
+  int soft_kind;
+  double eps2;
+  bool mixed;
+  const int32_t* leaf_cells;
+  const int32_t* leaf_rank;
+  Cells c;
+  PCols tp;
+  const float* lexp32;
+  const double* lexp64;
+  const int32_t *far_cnt, *far_idx, *near_cnt, *near_idx;
+  int64_t cap_far, cap_near;
+  const int32_t *tr_off, *tr_idx;       // transposed near lists (leaf ordinals)
+  double* ab;                           // cotangent in tree order (N x 3)
+  double* xbar;                         // tree order (N x 3)
+  double* mbar;                         // tree order (N)
+  double* cbar;                         // per leaf: 20 expansion cotangents
+  double* cell_bar;                     // per cell: M_bar, com_bar (3), Q_bar (6)
+};
+
+__global__ void k_gather_abar(const double* __restrict__ abar, VjpArgs V) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= V.n) return;
+  const int64_t i = V.tp.idx[p];
+  V.ab[3 * p] = abar[3 * i];
+  V.ab[3 * p + 1] = abar[3 * i + 1];
+  V.ab[3 * p + 2] = abar[3 * i + 2];
+  V.xbar[3 * p] = V.xbar[3 * p + 1] = V.xbar[3 * p + 2] = 0.0;
+  V.mbar[p] = 0.0;
+}
+
+__device__ __forceinline__ void load_coeffs(const VjpArgs& V, int k, double C[20]) {
+  if (V.mixed) {
+    const float* f = V.lexp32 + 24 * (int64_t)k;
+    for (int j = 0; j < 20; ++j) C[j] = (double)f[j];
+    for (int j = 0; j < 4; ++j) C[j] += (double)f[20 + j];
+  } else {
+    const double* d = V.lexp64 + 20 * (int64_t)k;
+    for (int j = 0; j < 20; ++j) C[j] = d[j];
+  }
+}
+
+// L2P reverse: warp per leaf, lane per particle.  a_i = -(C1 + C2 x + C3 x x / 2)
+// with x = x_i - com_alpha.
+__global__ void k_vjp_l2p(VjpArgs V) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= V.nleaves) return;
+  const int a = V.leaf_cells[k];
+  const int f = V.c.first[a], cnt = V.c.count[a];
+  double C[20];
+  load_coeffs(V, k, C);
+  double cb[20];
+  for (int j = 0; j < 20; ++j) cb[j] = 0.0;
+  double gx = 0.0, gy = 0.0, gz = 0.0;             // sum of (d a / d x)^T a_bar
+  if (lane < cnt) {
+    const int64_t p = (int64_t)f + lane;
+    const double x[3] = {V.tp.x[p] - V.c.cx[a], V.tp.y[p] - V.c.cy[a], V.tp.z[p] - V.c.cz[a]};
+    const double b[3] = {V.ab[3 * p], V.ab[3 * p + 1], V.ab[3 * p + 2]};
+    // (d a_i / d x_j) = -(C2_ij + C3_ijk x_k): g_j = sum_i b_i (d a_i / d x_j)
+    double g[3];
+    for (int jj = 0; jj < 3; ++jj) {
+      double s = 0.0;
+      for (int ii = 0; ii < 3; ++ii) {
+        double t = C[c2i(ii, jj)];
+        for (int kk = 0; kk < 3; ++kk) t += C[c3i(ii, jj, kk)] * x[kk];
+        s += b[ii] * t;
+      }
+      g[jj] = -s;
+    }
+    V.xbar[3 * p] += g[0];
+    V.xbar[3 * p + 1] += g[1];
+    V.xbar[3 * p + 2] += g[2];
+    gx = g[0]; gy = g[1]; gz = g[2];
+    // expansion cotangents: a_i depends on C1_i, C2_ij x_j, 1/2 C3_ijk x_j x_k
+    for (int ii = 0; ii < 3; ++ii) {
+      cb[1 + ii] -= b[ii];
+      for (int jj = 0; jj < 3; ++jj) {
+        cb[c2i(ii, jj)] -= b[ii] * x[jj];
+        for (int kk = 0; kk < 3; ++kk) cb[c3i(ii, jj, kk)] -= 0.5 * b[ii] * x[jj] * x[kk];
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int j = 0; j < 20; ++j) cb[j] += __shfl_xor_sync(0xffffffffu, cb[j], o);
+    gx += __shfl_xor_sync(0xffffffffu, gx, o);
+    gy += __shfl_xor_sync(0xffffffffu, gy, o);
+    gz += __shfl_xor_sync(0xffffffffu, gz, o);
+  }
+  if (lane == 0) {
+    for (int j = 0; j < 20; ++j) V.cbar[20 * (int64_t)k + j] = cb[j];
+    // x = x_i - com_alpha: the com receives minus the particles' share
+    double* cbc = V.cell_bar + 10 * (int64_t)a;
+    atomicAdd(&cbc[1], -gx);
+    atomicAdd(&cbc[2], -gy);
+    atomicAdd(&cbc[3], -gz);
+  }
+}
+
+// M2L reverse: warp per sink leaf, lanes over its far cells.
+__global__ void k_vjp_m2l(VjpArgs V) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= V.nleaves) return;
+  const int a = V.leaf_cells[k];
+  double cb[20];
+  for (int j = 0; j < 20; ++j) cb[j] = V.cbar[20 * (int64_t)k + j];
+  const double ax = V.c.cx[a], ay = V.c.cy[a], az = V.c.cz[a];
+  double rx = 0.0, ry = 0.0, rz = 0.0;
+  const int64_t off = (int64_t)k * V.cap_far;
+  const int nf = V.far_cnt[k];
+  const double zq[6] = {0, 0, 0, 0, 0, 0};
+  for (int e = lane; e < nf; e += 32) {
+    const int b = V.far_idx[off + e];
+    const double r[3] = {ax - V.c.cx[b], ay - V.c.cy[b], az - V.c.cz[b]};
+    const double* Qb = V.c.Q + 6 * (int64_t)b;
+    // r-derivatives
+    Dual3 R[3] = {Dual3{r[0], {1.0, 0.0, 0.0}}, Dual3{r[1], {0.0, 1.0, 0.0}},
+                  Dual3{r[2], {0.0, 0.0, 1.0}}};
+    Dual3 Cd[20];
+    m2l_coeffs_t<Dual3>(R, V.c.M[b], Qb, Cd);
+    double gr[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < 20; ++j)
+      for (int d = 0; d < 3; ++d) gr[d] += cb[j] * Cd[j].d[d];
+    // M and Q enter linearly
+    double Cu[20];
+    m2l_coeffs_t<double>(r, 1.0, zq, Cu);
+    double mbar = 0.0;
+    for (int j = 0; j < 20; ++j) mbar += cb[j] * Cu[j];
+    double qbar[6];
+    for (int q = 0; q < 6; ++q) {
+      double eq[6] = {0, 0, 0, 0, 0, 0};
+      eq[q] = 1.0;
+      m2l_coeffs_t<double>(r, 0.0, eq, Cu);
+      double s = 0.0;
+      for (int j = 0; j < 20; ++j) s += cb[j] * Cu[j];
+      qbar[q] = s;
+    }
+    rx += gr[0]; ry += gr[1]; rz += gr[2];
+    double* cbb = V.cell_bar + 10 * (int64_t)b;
+    atomicAdd(&cbb[0], mbar);
+    atomicAdd(&cbb[1], -gr[0]);
+    atomicAdd(&cbb[2], -gr[1]);
+    atomicAdd(&cbb[3], -gr[2]);
+    for (int q = 0; q < 6; ++q) atomicAdd(&cbb[4 + q], qbar[q]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rx += __shfl_xor_sync(0xffffffffu, rx, o);
+    ry += __shfl_xor_sync(0xffffffffu, ry, o);
+    rz += __shfl_xor_sync(0xffffffffu, rz, o);
+  }
+  if (lane == 0) {
+    double* cba = V.cell_bar + 10 * (int64_t)a;
+    atomicAdd(&cba[1], rx);
+    atomicAdd(&cba[2], ry);
+    atomicAdd(&cba[3], rz);
+  }
+}
+
+// Pair kernel K (a_i += m_j K(d), d = x_i - x_j) and (J b) for J = dK/dd.
+__device__ __forceinline__ double m4_F(double q) {
+  if (q < 1.0) return q * q * q * (4.0 / 3.0 - 1.2 * q * q + 0.5 * q * q * q);
+  if (q < 2.0) { const double t = 2.0 - q; return 1.0 - t * t * t * t * (1.0 - 0.8 * t + t * t / 6.0); }
+  return 1.0;
+}
+__device__ __forceinline__ double m4_w4pi(double q) {      // 4 pi w(q)
+  if (q < 1.0) return 4.0 * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
+  if (q < 2.0) { const double t = 2.0 - q; return t * t * t; }
+  return 0.0;
+}
+// K(d) = -f(r) d with J = dK/dd = -f I - g d d^T, g = f'(r) / r.  Plummer:
+// f = (r^2 + eps^2)^(-3/2).  M4 (Eq. 13, symmetrised): the mean of the two
+// sides' F(q) / (q^3 h^3) inside the support (1/r^3 outside), whose r-derivative
+// over r is (F'(q) q - 3 F(q)) / (q^5 h^5) with F' = 4 pi w q^2; at r = 0 the
+// side's f is 4 / (3 h^3) and its g is finite and multiplies d = 0.
+__device__ __forceinline__ void pair_fg(int kind, double r2, double eps2, double hi, double hj,
+                                        double& f, double& g) {
+  if (kind == KDFMM_SOFT_PLUMMER) {
+    const double s2 = r2 + eps2;
+    const double inv = 1.0 / sqrt(s2);
+    const double inv3 = inv * inv * inv;
+    f = inv3;
+    g = -3.0 * inv3 * inv * inv;
+    return;
+  }
+  const double r = sqrt(r2);
+  double fs = 0.0, gs = 0.0;
+  const double hs[2] = {hi, hj};
+  for (int side = 0; side < 2; ++side) {
+    const double h = hs[side];
+    const double q = r / h;
+    if (q >= 2.0) {
+      fs += 1.0 / (r2 * r);
+      gs += -3.0 / (r2 * r2 * r);
+    } else if (r2 == 0.0) {
+      fs += 4.0 / (3.0 * h * h * h);
+    } else {
+      const double h3 = h * h * h, q2 = q * q;
+      fs += m4_F(q) / (q2 * q * h3);
+      gs += (m4_w4pi(q) * q2 * q - 3.0 * m4_F(q)) / (q2 * q2 * q * h3 * h * h);
+    }
+  }
+  f = 0.5 * fs;
+  g = 0.5 * gs;
+}
+
+// P2P reverse, target side: x_bar_i += sum_j m_j J(d) a_bar_i.  Warp per leaf,
+// lanes = (target, slice).
+__global__ void k_vjp_p2p_target(VjpArgs V) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= V.nleaves) return;
+  const int a = V.leaf_cells[k];
+  const int fa = V.c.first[a], nt = V.c.count[a];
+  const int K = 32 / nt, t = lane % nt, sl = lane / nt;
+  const bool act = sl < K;
+  const int64_t pi = (int64_t)fa + t;
+  const double xi = V.tp.x[pi], yi = V.tp.y[pi], zi = V.tp.z[pi], hi = V.tp.h[pi];
+  const double b[3] = {V.ab[3 * pi], V.ab[3 * pi + 1], V.ab[3 * pi + 2]};
+  double gx = 0.0, gy = 0.0, gz = 0.0;
+  const int64_t e0 = (int64_t)k * V.cap_near;
+  const int nn = V.near_cnt[k];
+  if (act) {
+    for (int e = 0; e < nn; ++e) {
+      const int bc = V.near_idx[e0 + e];
+      const int fb = V.c.first[bc], nb = V.c.count[bc];
+      for (int j = sl; j < nb; j += K) {
+        const int64_t pj = (int64_t)fb + j;
+        if (pj == pi) continue;
+        const double d[3] = {xi - V.tp.x[pj], yi - V.tp.y[pj], zi - V.tp.z[pj]};
+        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double f, g;
+        pair_fg(V.soft_kind, r2, V.eps2, hi, V.tp.h[pj], f, g);
+        const double db = d[0] * b[0] + d[1] * b[1] + d[2] * b[2];
+        const double mj = V.tp.m[pj];
+        // J b = -f b - (f'/r) d (d.b)
+        gx += mj * (-f * b[0] - g * d[0] * db);
+        gy += mj * (-f * b[1] - g * d[1] * db);
+        gz += mj * (-f * b[2] - g * d[2] * db);
+      }
+    }
+  }
+  for (int s = 1; s < K; ++s) {
+    const int src = t + s * nt;
+    const double ox = __shfl_sync(0xffffffffu, gx, src), oy = __shfl_sync(0xffffffffu, gy, src),
+                 oz = __shfl_sync(0xffffffffu, gz, src);
+    if (sl == 0) { gx += ox; gy += oy; gz += oz; }
+  }
+  if (act && sl == 0) {
+    V.xbar[3 * pi] += gx;
+    V.xbar[3 * pi + 1] += gy;
+    V.xbar[3 * pi + 2] += gz;
+  }
+}
+
+// P2P reverse, source side: for source j, over the targets i whose near list
+// holds j's leaf: x_bar_j -= m_j J(d) a_bar_i, m_bar_j += K(d) . a_bar_i.
+__global__ void k_vjp_p2p_source(VjpArgs V) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // source leaf ordinal
+  const int lane = threadIdx.x & 31;
+  if (k >= V.nleaves) return;
+  const int bcell = V.leaf_cells[k];
+  const int fb = V.c.first[bcell], ns = V.c.count[bcell];
+  const int K = 32 / ns, j = lane % ns, sl = lane / ns;
+  const bool act = sl < K;
+  const int64_t pj = (int64_t)fb + j;
+  const double xj = V.tp.x[pj], yj = V.tp.y[pj], zj = V.tp.z[pj], hj = V.tp.h[pj], mj = V.tp.m[pj];
+  double gx = 0.0, gy = 0.0, gz = 0.0, gm = 0.0;
+  if (act) {
+    for (int e = V.tr_off[k]; e < V.tr_off[k + 1]; ++e) {
+      const int acell = V.leaf_cells[V.tr_idx[e]];
+      const int fa = V.c.first[acell], nt = V.c.count[acell];
+      for (int i = sl; i < nt; i += K) {
+        const int64_t pi = (int64_t)fa + i;
+        if (pi == pj) continue;
+        const double d[3] = {V.tp.x[pi] - xj, V.tp.y[pi] - yj, V.tp.z[pi] - zj};
+        const double b[3] = {V.ab[3 * pi], V.ab[3 * pi + 1], V.ab[3 * pi + 2]};
+        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double f, g;
+        pair_fg(V.soft_kind, r2, V.eps2, V.tp.h[pi], hj, f, g);
+        const double db = d[0] * b[0] + d[1] * b[1] + d[2] * b[2];
+        gx -= mj * (-f * b[0] - g * d[0] * db);
+        gy -= mj * (-f * b[1] - g * d[1] * db);
+        gz -= mj * (-f * b[2] - g * d[2] * db);
+        gm += -f * db;                                       // K(d) . b
+      }
+    }
+  }
+  for (int s = 1; s < K; ++s) {
+    const int src = j + s * ns;
+    const double ox = __shfl_sync(0xffffffffu, gx, src), oy = __shfl_sync(0xffffffffu, gy, src),
+                 oz = __shfl_sync(0xffffffffu, gz, src), om = __shfl_sync(0xffffffffu, gm, src);
+    if (sl == 0) { gx += ox; gy += oy; gz += oz; gm += om; }
+  }
+  if (act && sl == 0) {
+    V.xbar[3 * pj] += gx;
+    V.xbar[3 * pj + 1] += gy;
+    V.xbar[3 * pj + 2] += gz;
+    V.mbar[pj] += gm;
+  }
+}
+
+// Moments reverse.  For a cell with cotangents (M_bar, com_bar, Q_bar):
+// com = S / M gives S_bar = com_bar / M and M_bar' = M_bar - com_bar.com / M;
+// Q (Eq. 7) gives, with G = [[4q0-2q3-2q5, 3q1, 3q2], [., 4q3-2q0-2q5, 3q4],
+// [., ., 4q5-2q0-2q3]] and y = x - com:
+//   m_bar_i += M_bar' + x.S_bar + y^T G y / 2,   x_bar_i += m_i (S_bar + G y).
+// As polynomials in x: a0 + a1.x + x^T (G/2) x and m_i (a1 + G x), with
+// a1 = S_bar - G com, a0 = M_bar' + com^T G com / 2; summed over ancestors.
+__global__ void k_vjp_moments(VjpArgs V) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= V.nleaves) return;
+  const int leaf = V.leaf_cells[k];
+  double a0 = 0.0, a1[3] = {0.0, 0.0, 0.0}, G[6] = {0, 0, 0, 0, 0, 0};   // G: xx xy xz yy yz zz
+  for (int c = leaf; c >= 0; c = V.c.parent[c]) {
+    const double* cb = V.cell_bar + 10 * (int64_t)c;
+    const double M = V.c.M[c];
+    const double com[3] = {V.c.cx[c], V.c.cy[c], V.c.cz[c]};
+    const double Sb[3] = {cb[1] / M, cb[2] / M, cb[3] / M};
+    const double Mb = cb[0] - (cb[1] * com[0] + cb[2] * com[1] + cb[3] * com[2]) / M;
+    const double q0 = cb[4], q1 = cb[5], q2 = cb[6], q3 = cb[7], q4 = cb[8], q5 = cb[9];
+    const double g[6] = {4 * q0 - 2 * q3 - 2 * q5, 3 * q1, 3 * q2, 4 * q3 - 2 * q0 - 2 * q5, 3 * q4,
+                         4 * q5 - 2 * q0 - 2 * q3};
+    const double Gc[3] = {g[0] * com[0] + g[1] * com[1] + g[2] * com[2],
+                          g[1] * com[0] + g[3] * com[1] + g[4] * com[2],
+                          g[2] * com[0] + g[4] * com[1] + g[5] * com[2]};
+    a0 += Mb + 0.5 * (com[0] * Gc[0] + com[1] * Gc[1] + com[2] * Gc[2]);
+    for (int d = 0; d < 3; ++d) a1[d] += Sb[d] - Gc[d];
+    for (int d = 0; d < 6; ++d) G[d] += g[d];
+  }
+  const int f = V.c.first[leaf], cnt = V.c.count[leaf];
+  for (int j = 0; j < cnt; ++j) {
+    const int64_t p = (int64_t)f + j;
+    const double x[3] = {V.tp.x[p], V.tp.y[p], V.tp.z[p]};
+    const double Gx[3] = {G[0] * x[0] + G[1] * x[1] + G[2] * x[2],
+                          G[1] * x[0] + G[3] * x[1] + G[4] * x[2],
+                          G[2] * x[0] + G[4] * x[1] + G[5] * x[2]};
+    const double mi = V.tp.m[p];
+    V.mbar[p] += a0 + a1[0] * x[0] + a1[1] * x[1] + a1[2] * x[2] +
+                 0.5 * (x[0] * Gx[0] + x[1] * Gx[1] + x[2] * Gx[2]);
+    V.xbar[3 * p] += mi * (a1[0] + Gx[0]);
+    V.xbar[3 * p + 1] += mi * (a1[1] + Gx[1]);
+    V.xbar[3 * p + 2] += mi * (a1[2] + Gx[2]);
+  }
+}
+
+__global__ void k_scatter_bar(VjpArgs V, double* __restrict__ x_bar, double* __restrict__ m_bar) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= V.n) return;
+  const int64_t i = V.tp.idx[p];
+  x_bar[3 * i] = V.xbar[3 * p];
+  x_bar[3 * i + 1] = V.xbar[3 * p + 1];
+  x_bar[3 * i + 2] = V.xbar[3 * p + 2];
+  m_bar[i] = V.mbar[p];
+}
+
+// Transposed near lists: count, offsets, fill, then each leaf's list sorted.
+__global__ void k_tr_count(VjpArgs V, int32_t* cnt) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= V.nleaves) return;
+  const int64_t e0 = (int64_t)k * V.cap_near;
+  for (int e = 0; e < V.near_cnt[k]; ++e) atomicAdd(&cnt[V.leaf_rank[V.near_idx[e0 + e]]], 1);
+}
+__global__ void k_tr_fill(VjpArgs V, const int32_t* off, int32_t* cursor, int32_t* idx) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= V.nleaves) return;
+  const int64_t e0 = (int64_t)k * V.cap_near;
+  for (int e = 0; e < V.near_cnt[k]; ++e) {
+    const int b = V.leaf_rank[V.near_idx[e0 + e]];
+    idx[off[b] + atomicAdd(&cursor[b], 1)] = k;
+  }
+}
+__global__ void k_tr_sort(const int32_t* off, int32_t* idx, int nleaves) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nleaves) return;
+  const int lo = off[k], hi = off[k + 1];
+  for (int i = lo + 1; i < hi; ++i) {                 // insertion sort (short lists)
+    const int v = idx[i];
+    int j = i - 1;
+    while (j >= lo && idx[j] > v) { idx[j + 1] = idx[j]; --j; }
+    idx[j + 1] = v;
+  }
+}
+
+}  // namespace
+
+int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, cudaStream_t s) {
+  const int64_t n = t->n;
+  const int nl = t->nleaves, nc = t->ncells;
+  // scratch: a_bar, x_bar, m_bar in tree order, expansion and cell cotangents, transposed lists
+  const int64_t nnear = t->host_stats[KDFMM_STAT_NNEAR];
+  const size_t bytes = (size_t)n * 7 * sizeof(double) + (size_t)nl * 20 * sizeof(double) +
+                       (size_t)nc * 10 * sizeof(double) + (size_t)(3 * (nl + 2) + nnear + 16) * sizeof(int32_t);
+  char* buf = nullptr;
+  int rc = check_cuda(cudaMallocAsync((void**)&buf, bytes, s), "adjoint scratch");
+  if (rc) return rc;
+  VjpArgs V{};
+  V.n = n;
+  V.nleaves = nl;
+  V.ncells = nc;
+  V.soft_kind = t->p.soft_kind;
+  V.eps2 = t->p.eps * t->p.eps;
+  V.mixed = t->p.precision == KDFMM_MIXED;
+  V.leaf_cells = t->leaf_cells;
+  V.leaf_rank = t->leaf_rank;
+  V.c = t->c;
+  V.tp = t->tp;
+  V.lexp32 = t->lexp32;
+  V.lexp64 = t->lexp64;
+  V.far_cnt = t->L.far_cnt; V.far_idx = t->L.far_idx;
+  V.near_cnt = t->L.near_cnt; V.near_idx = t->L.near_idx;
+  V.cap_far = t->L.cap_far; V.cap_near = t->L.cap_near;
+  double* dp = reinterpret_cast<double*>(buf);
+  V.ab = dp; dp += 3 * n;
+  V.xbar = dp; dp += 3 * n;
+  V.mbar = dp; dp += n;
+  V.cbar = dp; dp += 20 * (int64_t)nl;
+  V.cell_bar = dp; dp += 10 * (int64_t)nc;
+  int32_t* ip = reinterpret_cast<int32_t*>(dp);
+  int32_t* tcnt = ip; ip += nl + 2;
+  int32_t* toff = ip; ip += nl + 2;
+  int32_t* tcur = ip; ip += nl + 2;
+  int32_t* tidx = ip;
+  V.tr_off = toff;
+  V.tr_idx = tidx;
+  cudaMemsetAsync(V.cell_bar, 0, (size_t)nc * 10 * sizeof(double), s);
+  cudaMemsetAsync(tcnt, 0, (size_t)(nl + 2) * sizeof(int32_t), s);
+  cudaMemsetAsync(tcur, 0, (size_t)(nl + 2) * sizeof(int32_t), s);
+  k_gather_abar<<<blocks_for(n, 256), 256, 0, s>>>(a_bar, V);
+  k_tr_count<<<blocks_for(nl, 128), 128, 0, s>>>(V, tcnt);
+  scan_i32(tcnt, toff, nl, t->scan_tmp, s);
+  k_tr_fill<<<blocks_for(nl, 128), 128, 0, s>>>(V, toff, tcur, tidx);
+  k_tr_sort<<<blocks_for(nl, 128), 128, 0, s>>>(toff, tidx, nl);
+  k_vjp_l2p<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
+  k_vjp_m2l<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
+  k_vjp_p2p_target<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
+  k_vjp_p2p_source<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
+  k_vjp_moments<<<blocks_for(nl, 128), 128, 0, s>>>(V);
+  k_scatter_bar<<<blocks_for(n, 256), 256, 0, s>>>(V, x_bar, m_bar);
+  t->launches += 13;
+  rc = check_cuda(cudaGetLastError(), "adjoint launch");
+  cudaFreeAsync(buf, s);
+  return rc;
+}
+
+}  // namespace kdfmm

@@ -143,6 +143,13 @@ def tree_build(tree, x, m, h, params: Params, stream=None) -> None:
 
 
 def tree_moments(tree, x, m, h, stream=None) -> None:
+    """New positions / masses / smoothing lengths of the same particles on the
+    built tree (frozen topology and interaction lists); see include/kdfmm.h."""
+    n = x.shape[0]
+    _dev_f64(x, "x", (n, 3))
+    _dev_f64(m, "m", (n,))
+    if h is not None:
+        _dev_f64(h, "h", (n,))
     _check(lib().kdfmm_tree_moments(tree, _ptr(x), _ptr(m), _ptr(h), _stream(stream)),
            "tree_moments")
 
@@ -155,6 +162,12 @@ def fmm_accel(tree, a, phi=None, stream=None) -> None:
 
 
 def fmm_accel_vjp(tree, a_bar, x_bar, m_bar, stream=None) -> None:
+    """x_bar (n,3), m_bar (n,) = (d a / d x)^T a_bar, (d a / d m)^T a_bar of the
+    last evaluation, lists and topology held fixed."""
+    n = a_bar.shape[0]
+    _dev_f64(a_bar, "a_bar", (n, 3))
+    _dev_f64(x_bar, "x_bar", (n, 3))
+    _dev_f64(m_bar, "m_bar", (n,))
     _check(lib().kdfmm_fmm_accel_vjp(tree, _ptr(a_bar), _ptr(x_bar), _ptr(m_bar), _stream(stream)),
            "fmm_accel_vjp")
 
@@ -262,6 +275,20 @@ class KdFmm:
             phi = torch.empty(self.n, dtype=torch.float64, device="cuda")
         fmm_accel(self.handle, a, phi, stream)
         return a, phi
+
+    def moments(self, x, m, h=None, stream=None):
+        """Refresh the cell moments for moved particles; the next accel() reuses
+        the topology and interaction lists of the last walk."""
+        tree_moments(self.handle, x, m, h, stream)
+        return self
+
+    def vjp(self, a_bar, stream=None):
+        """(x_bar, m_bar) of the last accel() for the cotangent a_bar (n, 3)."""
+        import torch
+        x_bar = torch.empty((self.n, 3), dtype=torch.float64, device="cuda")
+        m_bar = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        fmm_accel_vjp(self.handle, a_bar, x_bar, m_bar, stream)
+        return x_bar, m_bar
 
     def stats(self) -> dict:
         return tree_stats(self.handle)
