@@ -243,6 +243,23 @@ def traffic_for(kernel_key):
     return rec.get("bytes_per_launch_full_size")
 
 
+def reduce_max(value: float, dev, world: int) -> float:
+    """Largest value over the ranks (the slowest replica sets the job's time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(n_per_rank: int, steps: int, max_total_ms: float, world: int) -> float:
+    """Mparticles/s of the whole job: every rank evaluates its own replica of
+    n_per_rank particles per step; the job takes the slowest rank's time."""
+    return world * n_per_rank * steps / (max_total_ms / 1e3) / 1e6
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -310,13 +327,9 @@ def run_ours(args):
     native.tree_timing(f.handle, False, read=False)
     st = f.stats()
     launches = st["launches"] - launches0 + 2 * args.steps      # + the two momentum kernels per step
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(sum(times), dev, world)
     ms_per_step = total_ms / args.steps
-    value = world * n * args.steps / (total_ms / 1e3) / 1e6
+    value = whole_job_rate(n, args.steps, total_ms, world)
 
     # dominant kernel: P2P (+ L2P + assembly), one launch per step
     p2p_mean = statistics.mean(p2p_ms)
@@ -392,12 +405,8 @@ def run_ours(args):
             e1.record(stream)
             e1.synchronize()
             te.append(e0.elapsed_time(e1))
-        ems = sum(te)
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * n * args.steps / (ems / 1e3) / 1e6, "unit": UNIT,
+        ems = reduce_max(sum(te), dev, world)
+        e2e = {"value": whole_job_rate(n, args.steps, ems, world), "unit": UNIT,
                "h2d_bytes_per_step": int(n * (24 + 8 + (8 if h is not None else 0))),
                "d2h_bytes_per_step": int(n * 24 + 24), "ms_per_step": ems / args.steps}
 
