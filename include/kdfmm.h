@@ -108,6 +108,35 @@ void kdfmm_tree_destroy(kdfmm_tree t);
 int kdfmm_tree_build(kdfmm_tree t, const double* x, const double* m, const double* h, int64_t n,
                      const kdfmm_params* p, void* stream);
 
+/* A forest of independent systems in one handle: system k is particles
+ * [sys_offset[k], sys_offset[k+1]) of x, m, h, with its own opening parameter
+ * theta[k], softening length eps[k] and leaf size n_leaf[k] (Sec. 2 applied
+ * to each system alone; the paper evaluates one system at a time).  Each
+ * system's tree is exactly the tree kdfmm_tree_build makes for it alone;
+ * every phase of the build and of kdfmm_fmm_accel processes all systems in
+ * the same launches, and a leaf's walk never leaves its own tree.
+ * sys_offset (n_sys + 1 entries, sys_offset[0] = 0, strictly increasing, total
+ * <= 2^30), theta, eps and n_leaf (n_sys entries each) are HOST arrays; a
+ * NULL theta / eps / n_leaf takes p->theta / p->eps / p->n_leaf for every
+ * system.  p->soft_kind, p->precision and p->r_kern apply to all systems.
+ * Cells are numbered in pre-order system after system: system k's cells are
+ * the contiguous range starting at its root (the cells with parent -1, in
+ * system order); kdfmm_tree_export returns the whole forest.  Synchronises
+ * `stream`.  Errors as kdfmm_tree_build, and KDFMM_ERR_INVALID_ARG for an
+ * empty system, a decreasing offset or a parameter out of range. */
+int kdfmm_forest_build(kdfmm_tree t, const double* x, const double* m, const double* h,
+                       const int64_t* sys_offset, int32_t n_sys, const double* theta,
+                       const double* eps, const int32_t* n_leaf, const kdfmm_params* p,
+                       void* stream);
+
+/* kdfmm_forest_build followed by kdfmm_fmm_accel: accelerations a (N x 3) and
+ * potentials phi (N or NULL) of every system, in caller order, each system
+ * feeling only its own particles. */
+int kdfmm_fmm_accel_batched(kdfmm_tree t, const double* x, const double* m, const double* h,
+                            const int64_t* sys_offset, int32_t n_sys, const double* theta,
+                            const double* eps, const int32_t* n_leaf, const kdfmm_params* p,
+                            double* a, double* phi, void* stream);
+
 /* Moments for a frozen tree (Sec. 2; Eq. 7): recomputes M, centre of mass, s,
  * h_max and Q of the existing cells for new positions / masses / smoothing
  * lengths of the same particles (same caller order and n), and freezes the

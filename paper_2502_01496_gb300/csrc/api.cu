@@ -1,6 +1,7 @@
 // C ABI of the kdfmm library (declared in include/kdfmm.h): argument
 // checking, device buffers owned by the handle, and the order of the steps of
 // one force evaluation.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -91,6 +92,111 @@ static int grow_eval_buffers(kdfmm_tree_s* t, int64_t cap) {
   return KDFMM_OK;
 }
 
+// Per-system parameters on the device (a single tree is a forest of one).
+// Host arrays are staged through pinned memory owned by the handle.
+static int set_systems(kdfmm_tree_s* t, const int64_t* off, int32_t n_sys, const double* theta,
+                       const double* eps, const int32_t* nleaf, const kdfmm_params* p,
+                       cudaStream_t s) {
+  if (n_sys > t->cap_sys) {
+    cudaStreamSynchronize(s);
+    cudaFree(t->sys_off); cudaFree(t->sys_theta); cudaFree(t->sys_eps); cudaFree(t->sys_nleaf);
+    cudaFree(t->sys_root);
+    if (t->host_sys_off) cudaFreeHost(t->host_sys_off);
+    t->sys_off = nullptr; t->sys_theta = t->sys_eps = nullptr;
+    t->sys_nleaf = t->sys_root = nullptr;
+    t->host_sys_off = nullptr;
+    t->cap_sys = 0;
+    t->n_sys = 0;
+    const size_t k = (size_t)n_sys + 1;
+    if (cudaMalloc(&t->sys_off, k * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&t->sys_theta, k * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&t->sys_eps, k * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&t->sys_nleaf, k * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&t->sys_root, k * sizeof(int32_t)) != cudaSuccess ||
+        cudaHostAlloc(&t->host_sys_off, k * (2 * sizeof(int64_t) + 2 * sizeof(double)), 0) !=
+            cudaSuccess)
+      return set_error(KDFMM_ERR_OOM, "system tables (%d systems)", n_sys);
+    t->cap_sys = n_sys;
+  }
+  const size_t k = (size_t)t->cap_sys + 1;
+  int64_t* ho = t->host_sys_off;
+  double* ht = reinterpret_cast<double*>(ho + k);
+  double* he = ht + k;
+  int32_t* hn = reinterpret_cast<int32_t*>(he + k);
+  // the staged copy of the previous call has completed (every build synchronises)
+  bool same = t->n_sys == n_sys;
+  for (int32_t i = 0; same && i <= n_sys; ++i) same = ho[i] == off[i];
+  for (int32_t i = 0; same && i < n_sys; ++i)
+    same = ht[i] == (theta ? theta[i] : p->theta) && he[i] == (eps ? eps[i] : p->eps) &&
+           hn[i] == (nleaf ? nleaf[i] : p->n_leaf);
+  if (same) return KDFMM_OK;
+  int32_t mn = KDFMM_MAX_LEAF;
+  for (int32_t i = 0; i <= n_sys; ++i) ho[i] = off[i];
+  for (int32_t i = 0; i < n_sys; ++i) {
+    ht[i] = theta ? theta[i] : p->theta;
+    he[i] = eps ? eps[i] : p->eps;
+    hn[i] = nleaf ? nleaf[i] : p->n_leaf;
+    mn = std::min(mn, hn[i]);
+  }
+  t->n_sys = n_sys;
+  t->min_nleaf = mn;
+  int rc = check_cuda(cudaMemcpyAsync(t->sys_off, ho, k * sizeof(int64_t), cudaMemcpyHostToDevice, s),
+                      "system offsets");
+  if (!rc) rc = check_cuda(cudaMemcpyAsync(t->sys_theta, ht, n_sys * sizeof(double),
+                                           cudaMemcpyHostToDevice, s), "system theta");
+  if (!rc) rc = check_cuda(cudaMemcpyAsync(t->sys_eps, he, n_sys * sizeof(double),
+                                           cudaMemcpyHostToDevice, s), "system eps");
+  if (!rc) rc = check_cuda(cudaMemcpyAsync(t->sys_nleaf, hn, n_sys * sizeof(int32_t),
+                                           cudaMemcpyHostToDevice, s), "system n_leaf");
+  return rc;
+}
+
+static int check_systems(const int64_t* off, int32_t n_sys, const double* theta, const double* eps,
+                         const int32_t* nleaf) {
+  if (n_sys < 1) return set_error(KDFMM_ERR_INVALID_ARG, "n_sys must be >= 1 (got %d)", n_sys);
+  if (!off) return set_error(KDFMM_ERR_INVALID_ARG, "sys_offset is NULL");
+  if (off[0] != 0) return set_error(KDFMM_ERR_INVALID_ARG, "sys_offset[0] must be 0");
+  for (int32_t i = 0; i < n_sys; ++i) {
+    if (off[i + 1] <= off[i])
+      return set_error(KDFMM_ERR_INVALID_ARG, "system %d is empty or sys_offset decreases", i);
+    if (theta && !(theta[i] >= 0.0 && theta[i] <= 1.0))
+      return set_error(KDFMM_ERR_INVALID_ARG, "theta[%d] must lie in [0, 1] (got %g)", i, theta[i]);
+    if (eps && !(std::isfinite(eps[i]) && eps[i] >= 0.0))
+      return set_error(KDFMM_ERR_INVALID_ARG, "eps[%d] must be finite and >= 0", i);
+    if (nleaf && (nleaf[i] < 1 || nleaf[i] > KDFMM_MAX_LEAF))
+      return set_error(KDFMM_ERR_INVALID_ARG, "n_leaf[%d] must lie in [1, %d] (got %d)", i,
+                       KDFMM_MAX_LEAF, nleaf[i]);
+  }
+  if (off[n_sys] > (int64_t(1) << 30))
+    return set_error(KDFMM_ERR_INVALID_ARG, "total particle count above 2^30");
+  return KDFMM_OK;
+}
+
+// Builds the forest whose systems set_systems has just described.
+static int build_common(kdfmm_tree_s* t, const double* x, const double* m, const double* h,
+                        int64_t n, const kdfmm_params* p, cudaStream_t s) {
+  t->built = t->evaluated = t->lists_frozen = false;
+  t->n = n;
+  t->p = *p;
+  const int64_t old_cap = t->cap_n;
+  int rc;
+  phase_begin(t, KDFMM_PHASE_BUILD, s);
+  if ((rc = build_tree(t, x, m, h, s))) return rc;
+  phase_end(t, KDFMM_PHASE_BUILD, s);
+  if (t->cap_n != old_cap || t->L.far_cnt == nullptr)
+    if ((rc = grow_eval_buffers(t, t->cap_n))) return rc;
+  t->built = true;
+  int64_t* hs = t->host_stats;
+  hs[KDFMM_STAT_N] = n;
+  hs[KDFMM_STAT_NCELLS] = t->ncells;
+  hs[KDFMM_STAT_NLEAVES] = t->nleaves;
+  hs[KDFMM_STAT_DEPTH] = t->depth;
+  hs[KDFMM_STAT_NFAR] = hs[KDFMM_STAT_NNEAR] = hs[KDFMM_STAT_NP2P] = 0;
+  hs[KDFMM_STAT_NFALLBACK] = t->nfallback;
+  hs[KDFMM_STAT_NEXACT] = 0;
+  return KDFMM_OK;
+}
+
 }  // namespace kdfmm
 
 using namespace kdfmm;
@@ -131,6 +237,9 @@ void kdfmm_tree_destroy(kdfmm_tree t) {
   cudaFree(t->L.far_cnt); cudaFree(t->L.near_cnt); cudaFree(t->L.far_off); cudaFree(t->L.near_off);
   cudaFree(t->L.far_idx); cudaFree(t->L.near_idx); cudaFree(t->L.near_np);
   cudaFree(t->mom_partial);
+  cudaFree(t->sys_off); cudaFree(t->sys_theta); cudaFree(t->sys_eps); cudaFree(t->sys_nleaf);
+  cudaFree(t->sys_root);
+  if (t->host_sys_off) cudaFreeHost(t->host_sys_off);
   for (cudaEvent_t& e : t->ev)
     if (e) cudaEventDestroy(e);
   if (t->host_stats) cudaFreeHost(t->host_stats);
@@ -153,25 +262,37 @@ int kdfmm_tree_build(kdfmm_tree t, const double* x, const double* m, const doubl
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev != t->device) return set_error(KDFMM_ERR_INVALID_ARG, "handle belongs to device %d", t->device);
-  t->built = t->evaluated = t->lists_frozen = false;
-  t->n = n;
-  t->p = *p;
-  const int64_t old_cap = t->cap_n;
-  phase_begin(t, KDFMM_PHASE_BUILD, s);
-  if ((rc = build_tree(t, x, m, h, s))) return rc;
-  phase_end(t, KDFMM_PHASE_BUILD, s);
-  if (t->cap_n != old_cap || t->L.far_cnt == nullptr)
-    if ((rc = grow_eval_buffers(t, t->cap_n))) return rc;
-  t->built = true;
-  int64_t* hs = t->host_stats;
-  hs[KDFMM_STAT_N] = n;
-  hs[KDFMM_STAT_NCELLS] = t->ncells;
-  hs[KDFMM_STAT_NLEAVES] = t->nleaves;
-  hs[KDFMM_STAT_DEPTH] = t->depth;
-  hs[KDFMM_STAT_NFAR] = hs[KDFMM_STAT_NNEAR] = hs[KDFMM_STAT_NP2P] = 0;
-  hs[KDFMM_STAT_NFALLBACK] = t->nfallback;
-  hs[KDFMM_STAT_NEXACT] = 0;
-  return KDFMM_OK;
+  const int64_t off[2] = {0, n};
+  if ((rc = set_systems(t, off, 1, nullptr, nullptr, nullptr, p, s))) return rc;
+  return build_common(t, x, m, h, n, p, s);
+}
+
+int kdfmm_forest_build(kdfmm_tree t, const double* x, const double* m, const double* h,
+                       const int64_t* sys_offset, int32_t n_sys, const double* theta,
+                       const double* eps, const int32_t* n_leaf, const kdfmm_params* p,
+                       void* stream) {
+  // host-side arguments first: they need no device
+  int rc = check_params(p, h);
+  if (rc) return rc;
+  if ((rc = check_systems(sys_offset, n_sys, theta, eps, n_leaf))) return rc;
+  if (!t) return set_error(KDFMM_ERR_INVALID_ARG, "tree is NULL");
+  if (!is_device_ptr(x) || !is_device_ptr(m) || (h != nullptr && !is_device_ptr(h)))
+    return set_error(KDFMM_ERR_INVALID_ARG, "x, m (and h) must be device pointers");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return set_error(KDFMM_ERR_INVALID_ARG, "handle belongs to device %d", t->device);
+  if ((rc = set_systems(t, sys_offset, n_sys, theta, eps, n_leaf, p, s))) return rc;
+  return build_common(t, x, m, h, sys_offset[n_sys], p, s);
+}
+
+int kdfmm_fmm_accel_batched(kdfmm_tree t, const double* x, const double* m, const double* h,
+                            const int64_t* sys_offset, int32_t n_sys, const double* theta,
+                            const double* eps, const int32_t* n_leaf, const kdfmm_params* p,
+                            double* a, double* phi, void* stream) {
+  int rc = kdfmm_forest_build(t, x, m, h, sys_offset, n_sys, theta, eps, n_leaf, p, stream);
+  if (rc) return rc;
+  return kdfmm_fmm_accel(t, a, phi, stream);
 }
 
 int kdfmm_tree_moments(kdfmm_tree t, const double* x, const double* m, const double* h,

@@ -30,9 +30,15 @@ struct BuildArgs {
   TmpCells tmp;
   int32_t* counters;
   int32_t* status;
-  int32_t n_leaf;
+  const int64_t* sys_off;          // forest: particle offsets of the systems
+  const int32_t* sys_nleaf;        // forest: leaf size of each system
+  int32_t n_sys;
   int64_t capA, capB, capL, cap_cells;
 };
+
+__device__ __forceinline__ int nleaf_at(const BuildArgs& A, int64_t first) {
+  return A.sys_nleaf[system_of(A.sys_off, A.n_sys, first)];
+}
 
 __device__ __forceinline__ double coord(const PCols& p, int axis, int64_t i) {
   return axis == 0 ? p.x[i] : (axis == 1 ? p.y[i] : p.z[i]);
@@ -44,12 +50,14 @@ __device__ __forceinline__ void set_status(int32_t* status, int bits) { atomicOr
 // initial gather: caller order -> SoA buffer 0, with validation
 // ---------------------------------------------------------------------------
 __global__ void k_init(const double* __restrict__ x, const double* __restrict__ m,
-                       const double* __restrict__ h, int64_t n, double eps, int soft_kind,
-                       PCols b, int32_t* status) {
+                       const double* __restrict__ h, int64_t n, const int64_t* __restrict__ sys_off,
+                       int n_sys, const double* __restrict__ sys_eps, int soft_kind, PCols b,
+                       int32_t* status) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2], mi = m[i];
-  double hi = (h != nullptr && soft_kind == KDFMM_SOFT_M4) ? h[i] : eps;
+  double hi = (h != nullptr && soft_kind == KDFMM_SOFT_M4) ? h[i]
+                                                           : sys_eps[system_of(sys_off, n_sys, i)];
   bool ok = isfinite(xi) && isfinite(yi) && isfinite(zi) && isfinite(mi) && isfinite(hi) &&
             mi > 0.0 && (soft_kind == KDFMM_SOFT_M4 ? hi > 0.0 : hi >= 0.0);
   if (!ok) set_status(status, ST_NONFINITE);
@@ -57,13 +65,23 @@ __global__ void k_init(const double* __restrict__ x, const double* __restrict__ 
   b.idx[i] = (int32_t)i;
 }
 
-__global__ void k_root(int64_t n, int32_t n_leaf, Seg* segA, Seg* segB, Seg* segL,
-                       int32_t* counters) {
-  Seg g{0, (int32_t)n, 0, 0};
-  counters[0] = 1;
-  if (n > kSubtreeMax) { segA[0] = g; counters[1] = 1; }
-  else if (n > n_leaf) { segB[0] = g; counters[2] = 1; }
-  else { segL[0] = g; counters[3] = 1; }
+// One root segment per system (build-order cell k for system k).
+__global__ void k_roots(BuildArgs A, Seg* segA, Seg* segB, Seg* segL) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) atomicAdd(&A.counters[0], A.n_sys);
+  if (k >= A.n_sys) return;
+  const int64_t f = A.sys_off[k], cnt = A.sys_off[k + 1] - f;
+  const Seg g{(int32_t)f, (int32_t)cnt, k, 0};
+  if (cnt > kSubtreeMax) {
+    const int i = atomicAdd(&A.counters[1], 1);
+    if (i < A.capA) segA[i] = g; else set_status(A.status, ST_CAPACITY);
+  } else if (cnt > A.sys_nleaf[k]) {
+    const int i = atomicAdd(&A.counters[2], 1);
+    if (i < A.capB) segB[i] = g; else set_status(A.status, ST_CAPACITY);
+  } else {
+    const int i = atomicAdd(&A.counters[3], 1);
+    if (i < A.capL) segL[i] = g; else set_status(A.status, ST_CAPACITY);
+  }
 }
 
 // Pushes a new segment onto the list that will process it.
@@ -71,7 +89,7 @@ __device__ void push_child(const BuildArgs& A, Seg c, Seg* nextA, Seg* segB, Seg
   if (c.count > kSubtreeMax) {
     int k = atomicAdd(&A.counters[1], 1);
     if (k < A.capA) nextA[k] = c; else set_status(A.status, ST_CAPACITY);
-  } else if (c.count > A.n_leaf) {
+  } else if (c.count > nleaf_at(A, c.first)) {
     int k = atomicAdd(&A.counters[2], 1);
     if (k < A.capB) segB[k] = c; else set_status(A.status, ST_CAPACITY);
   } else {
@@ -509,12 +527,13 @@ struct Queues {
   int* nleaf;
   int4* leaves;
   int leafcap;
+  int n_leaf;      // leaf size of the subtree's system
 };
 
 // Pushes child `c` (local first, count, cell, depth) onto the queue that will
 // process it; called by one thread.
 __device__ __forceinline__ void push_local(const SubArgs& S, const Queues& Q, int4 c) {
-  if (c.y > S.A.n_leaf) {
+  if (c.y > Q.n_leaf) {
     int pos = atomicAdd(Q.qn_next, 1);
     if (pos < S.qcap) Q.q_next[pos] = c; else set_status(S.A.status, ST_CAPACITY);
   } else {
@@ -596,7 +615,7 @@ __device__ void split_thread(const SubArgs& S, const SubSmem& L, const Queues& Q
   depth_max = max(depth_max, depth + 1);
   const int clf[2] = {lf, lf + nl}, ccnt[2] = {nl, cnt - nl};
   for (int side = 0; side < 2; ++side) {
-    if (ccnt[side] > A.n_leaf) {
+    if (ccnt[side] > Q.n_leaf) {
       int pos = atomicAdd(Q.qn_next, 1);
       if (pos < S.qcap) Q.q_next[pos] = make_int4(clf[side], ccnt[side], cid + side, depth + 1);
       else set_status(A.status, ST_CAPACITY);
@@ -881,6 +900,7 @@ k_subtree(SubArgs S) {
   const PCols in = (g.dbuf & 1) ? S.buf1 : S.buf0;
   const int n = g.count;
   const int gfirst = g.first;
+  const int n_leaf = nleaf_at(S.A, gfirst);
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const double x = in.x[gfirst + k], y = in.y[gfirst + k], z = in.z[gfirst + k];
     L.x[k] = x; L.y[k] = y; L.z[k] = z;
@@ -901,7 +921,7 @@ k_subtree(SubArgs S) {
     if (threadIdx.x == 0) { qn[nxt] = 0; nleaf = 0; }
     __syncthreads();
     const int nq = qn[cur];
-    const Queues Q{&qn[nxt], L.q[nxt], &nleaf, leaves, leafcap};
+    const Queues Q{&qn[nxt], L.q[nxt], &nleaf, leaves, leafcap, n_leaf};
     // large cells: the whole CTA, one after the other
     for (int qi = 0; qi < nq; ++qi) {
       const int4 e = L.q[cur][qi];
@@ -1024,7 +1044,14 @@ __global__ void k_remap(TmpCells tmp, int ncells, const int32_t* __restrict__ st
   } else {
     c.left[id] = -1; c.right[id] = -1;
   }
-  if (id == 0) c.parent[0] = -1;
+  if (d == 0) c.parent[id] = -1;               // a system's root
+}
+
+// Pre-order id of each system's root; sys_root[n_sys] = number of cells.
+__global__ void k_sys_roots(const int64_t* __restrict__ sys_off, int n_sys,
+                            const int32_t* __restrict__ start_off, int32_t* sys_root) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k <= n_sys) sys_root[k] = start_off[sys_off[k]];
 }
 
 // Leaves: h_max and Q (Eq. 7) from their particles (one thread per leaf);
@@ -1109,11 +1136,17 @@ __global__ void k_derive_cells(Cells c, int ncells, float* com_bound) {
   atomicMax(reinterpret_cast<int*>(com_bound), __float_as_int(b));
 }
 
-__global__ void k_leaf_list(const Cells c, int ncells, int32_t* leaf_rank, int32_t* leaf_cells) {
+__global__ void k_leaf_list(const Cells c, int ncells, int32_t* leaf_rank, int32_t* leaf_cells,
+                            const int64_t* __restrict__ sys_off, int n_sys, int32_t* leaf_sys) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ncells) return;
-  if (c.left[t] < 0) leaf_cells[leaf_rank[t]] = t;
-  else leaf_rank[t] = -1;
+  if (c.left[t] < 0) {
+    const int r = leaf_rank[t];
+    leaf_cells[r] = t;
+    leaf_sys[r] = system_of(sys_off, n_sys, c.first[t]);
+  } else {
+    leaf_rank[t] = -1;
+  }
 }
 
 // Per-particle float32 data relative to the centre of mass of its leaf.
@@ -1165,7 +1198,8 @@ void free_build_buffers(kdfmm_tree_s* t) {
                   t->start_off, t->scan_tmp, t->pf, t->ph, t->c.first, t->c.count, t->c.left,
                   t->c.right, t->c.parent, t->c.skip, t->c.depth, t->c.M, t->c.cx, t->c.cy,
                   t->c.cz, t->c.s, t->c.hmax, t->c.Q, t->c.walk, t->c.walk2, t->c.src32,
-                  t->c.src64, t->c.ready, t->leaf_cells, t->leaf_rank, t->lexp64, t->lexp32};
+                  t->c.src64, t->c.ready, t->leaf_cells, t->leaf_rank, t->leaf_sys, t->lexp64,
+                  t->lexp32};
   for (void* p : ptrs) cudaFree(p);
   t->segB = t->segL = nullptr;
   t->chunk_seg = t->seg_chunk_off = t->chunk_left = t->chunk_loff = t->seg_axis = t->seg_nl = nullptr;
@@ -1177,7 +1211,7 @@ void free_build_buffers(kdfmm_tree_s* t) {
   t->cnt_start = t->min_depth = t->start_off = t->scan_tmp = nullptr;
   t->pf = t->ph = nullptr;
   t->c = Cells{};
-  t->leaf_cells = t->leaf_rank = nullptr;
+  t->leaf_cells = t->leaf_rank = t->leaf_sys = nullptr;
   t->lexp64 = nullptr;
   t->lexp32 = nullptr;
   t->cap_n = 0;
@@ -1239,6 +1273,7 @@ static int ensure_build_buffers(kdfmm_tree_s* t, int64_t n) {
   KD_ALLOC(c.ready, nc);
   KD_ALLOC(t->leaf_cells, nc);
   KD_ALLOC(t->leaf_rank, nc + 1);
+  KD_ALLOC(t->leaf_sys, nc);
   KD_ALLOC(t->lexp64, 20 * (n + 1));
   KD_ALLOC(t->lexp32, 24 * (n + 1));
   t->cap_n = n;
@@ -1253,16 +1288,18 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
   cudaMemsetAsync(t->counters, 0, 16 * sizeof(int32_t), s);
   cudaMemsetAsync(t->status, 0, sizeof(int32_t), s);
   cudaMemsetAsync(t->com_bound, 0, sizeof(float), s);
-  k_init<<<blocks_for(n, 256), 256, 0, s>>>(x, m, h, n, P.eps, P.soft_kind, t->buf[0], t->status);
-  k_root<<<1, 1, 0, s>>>(n, P.n_leaf, t->segA[0], t->segB, t->segL, t->counters);
-  t->launches += 2;
-
   BuildArgs A{};
   A.tmp = t->tmp;
   A.counters = t->counters;
   A.status = t->status;
-  A.n_leaf = P.n_leaf;
+  A.sys_off = t->sys_off;
+  A.sys_nleaf = t->sys_nleaf;
+  A.n_sys = t->n_sys;
   A.capA = t->capA; A.capB = t->capB; A.capL = t->capL; A.cap_cells = t->cap_cells;
+  k_init<<<blocks_for(n, 256), 256, 0, s>>>(x, m, h, n, t->sys_off, t->n_sys, t->sys_eps,
+                                            P.soft_kind, t->buf[0], t->status);
+  k_roots<<<blocks_for(t->n_sys, 128), 128, 0, s>>>(A, t->segA[0], t->segB, t->segL);
+  t->launches += 2;
 
   int32_t* hc = t->host_counters;
   rc = check_cuda(cudaMemcpyAsync(hc, t->counters, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
@@ -1321,7 +1358,7 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
   S.buf1 = t->buf[1];
   S.out = t->tp;
   S.segB = t->segB;
-  S.qcap = kSubtreeMax / (P.n_leaf + 1) + 2;
+  S.qcap = kSubtreeMax / (t->min_nleaf + 1) + 2;
   if (nB > 0) {
     size_t smem = 4 * kSubtreeMax * sizeof(double) + 3 * kSubtreeMax * sizeof(float) +
                   2 * kSubtreeMax * sizeof(uint16_t) + 4 * (size_t)S.qcap * sizeof(int4);
@@ -1361,7 +1398,10 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
   scan_i32(t->c.ready, t->leaf_rank, ncells, t->scan_tmp, s);
   cudaMemcpyAsync(&t->host_counters[17], t->leaf_rank + ncells, sizeof(int32_t),
                   cudaMemcpyDeviceToHost, s);
-  k_leaf_list<<<blocks_for(ncells, 256), 256, 0, s>>>(t->c, ncells, t->leaf_rank, t->leaf_cells);
+  k_leaf_list<<<blocks_for(ncells, 256), 256, 0, s>>>(t->c, ncells, t->leaf_rank, t->leaf_cells,
+                                                      t->sys_off, t->n_sys, t->leaf_sys);
+  k_sys_roots<<<blocks_for(t->n_sys + 1, 128), 128, 0, s>>>(t->sys_off, t->n_sys, t->start_off,
+                                                            t->sys_root);
   cudaMemcpyAsync(&t->host_counters[16], t->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   if ((rc = check_cuda(cudaStreamSynchronize(s), "build finalise"))) return rc;
   t->nleaves = t->host_counters[17];
@@ -1371,7 +1411,7 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
   k_upward<<<blocks_for((int64_t)t->nleaves, 128), 128, 0, s>>>(t->c, t->leaf_cells,
                                                                      t->nleaves, t->tp);
   k_derive_cells<<<blocks_for(ncells, 256), 256, 0, s>>>(t->c, ncells, t->com_bound);
-  t->launches += 13;
+  t->launches += 14;
   k_particles32<<<blocks_for((int64_t)t->nleaves * 32, 256), 256, 0, s>>>(
       t->c, t->leaf_cells, t->nleaves, t->tp, t->pf, t->ph);
   t->launches += 1;
@@ -1388,13 +1428,17 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
 namespace {
 
 __global__ void k_gather_frozen(const double* __restrict__ x, const double* __restrict__ m,
-                                const double* __restrict__ h, int64_t n, double eps, int soft_kind,
-                                PCols tp, int32_t* status) {
+                                const double* __restrict__ h, int64_t n,
+                                const int64_t* __restrict__ sys_off, int n_sys,
+                                const double* __restrict__ sys_eps, int soft_kind, PCols tp,
+                                int32_t* status) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int64_t i = tp.idx[p];
   const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2], mi = m[i];
-  const double hi = (h != nullptr && soft_kind == KDFMM_SOFT_M4) ? h[i] : eps;
+  const double hi = (h != nullptr && soft_kind == KDFMM_SOFT_M4)
+                        ? h[i]
+                        : sys_eps[system_of(sys_off, n_sys, i)];
   const bool ok = isfinite(xi) && isfinite(yi) && isfinite(zi) && isfinite(mi) && isfinite(hi) &&
                   mi > 0.0 && (soft_kind == KDFMM_SOFT_M4 ? hi > 0.0 : hi >= 0.0);
   if (!ok) atomicOr(status, ST_NONFINITE);
@@ -1529,8 +1573,8 @@ int recompute_moments(kdfmm_tree_s* t, const double* x, const double* m, const d
   const int ncells = t->ncells, nl = t->nleaves;
   cudaMemsetAsync(t->status, 0, sizeof(int32_t), s);
   cudaMemsetAsync(t->com_bound, 0, sizeof(float), s);
-  k_gather_frozen<<<blocks_for(n, 256), 256, 0, s>>>(x, m, h, n, t->p.eps, t->p.soft_kind, t->tp,
-                                                     t->status);
+  k_gather_frozen<<<blocks_for(n, 256), 256, 0, s>>>(x, m, h, n, t->sys_off, t->n_sys, t->sys_eps,
+                                                     t->p.soft_kind, t->tp, t->status);
   double *Sx = t->tmp.cx, *Sy = t->tmp.cy, *Sz = t->tmp.cz;     // free after the build
   k_leaf_frozen<<<blocks_for(nl, 128), 128, 0, s>>>(t->c, t->leaf_cells, nl, t->tp, Sx, Sy, Sz);
   cudaMemsetAsync(t->c.ready, 0, (size_t)ncells * sizeof(int32_t), s);

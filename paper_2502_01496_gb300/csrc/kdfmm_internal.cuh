@@ -118,6 +118,19 @@ struct kdfmm_tree_s {
   double* lexp64 = nullptr;        // 20 per leaf
   float* lexp32 = nullptr;         // 24 per leaf (20 coefficients + 4 low parts)
 
+  // systems: a forest of independent trees (one system for a single tree);
+  // system k owns particles [sys_off[k], sys_off[k + 1]) in caller order and
+  // cells [sys_root[k], sys_root[k + 1]) in pre-order
+  int32_t n_sys = 0, cap_sys = 0;
+  int32_t min_nleaf = 0;
+  int64_t* sys_off = nullptr;      // device, n_sys + 1
+  double* sys_theta = nullptr;     // device, n_sys
+  double* sys_eps = nullptr;       // device, n_sys
+  int32_t* sys_nleaf = nullptr;    // device, n_sys
+  int32_t* sys_root = nullptr;     // device, n_sys + 1
+  int32_t* leaf_sys = nullptr;     // device, system of each leaf ordinal
+  int64_t* host_sys_off = nullptr; // pinned host copy of sys_off
+
   double* mom_partial = nullptr;   // total_momentum scratch
   int64_t cap_mom = 0;
   int64_t* host_stats = nullptr;   // pinned host mirror
@@ -292,6 +305,17 @@ __device__ __forceinline__ void two_sum_d(double a, double b, double& s, double&
   s = __dadd_rn(a, b);
   double bb = __dsub_rn(s, a);
   e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// System holding particle position p (caller order) of a forest: the largest
+// k with off[k] <= p (every system holds at least one particle).
+__device__ __forceinline__ int system_of(const int64_t* __restrict__ off, int n_sys, int64_t p) {
+  int lo = 0, hi = n_sys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
 // ---------------------------------------------------------------------------

@@ -43,8 +43,8 @@ struct P2PArgs {
   const double* lexp64;
   const float4* walk;        // cell (com, s) float32
   const float2* walk2;       // cell (h_max, skip)
-  float eps2f;
-  double eps2;
+  const int32_t* leaf_sys;   // system of each leaf
+  const double* sys_eps;     // Plummer softening length of each system
   double* a;
   double* phi;
 };
@@ -208,13 +208,14 @@ __device__ __forceinline__ void l2p_tail(const T* C, T x, T y, T z, T& ax, T& ay
 template <int SOFT, bool SELF>
 __device__ __forceinline__ void near_leaf32(const P2PArgs& A, int fb, int nb, int sl, int K, int t,
                                             float xs, float ys, float zs, const float4& hi,
-                                            float& fx, float& fy, float& fz, float& fp) {
+                                            float eps2f, float& fx, float& fy, float& fz,
+                                            float& fp) {
   for (int j = sl; j < nb; j += K) {
     if (SELF && j == t) continue;
     const float4 s = A.pf[fb + j];
     float4 hj = make_float4(0.f, 0.f, 0.f, 0.f);
     if (SOFT == KDFMM_SOFT_M4) hj = A.ph[fb + j];
-    pair32<SOFT>(xs - s.x, ys - s.y, zs - s.z, s.w, hi, hj, A.eps2f, fx, fy, fz, fp);
+    pair32<SOFT>(xs - s.x, ys - s.y, zs - s.z, s.w, hi, hj, eps2f, fx, fy, fz, fp);
   }
 }
 
@@ -259,10 +260,13 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
   if (M4) hi = A.ph[fa + t];
   const float4 ca = A.src32[4 * a], cal = A.src32[4 * a + 1];
   const float sa = A.walk[a].w, hmax_a = A.walk2[a].x;
+  const double eps = A.sys_eps[A.leaf_sys[k]];
+  const float eps2f = (float)(eps * eps);
   float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, azh = 0.f, azl = 0.f, ph_ = 0.f, pl = 0.f;
   {
     float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;
-    if (act) near_leaf32<SOFT, true>(A, fa, nt, sl, K, t, xa.x, xa.y, xa.z, hi, fx, fy, fz, fp);
+    if (act)
+      near_leaf32<SOFT, true>(A, fa, nt, sl, K, t, xa.x, xa.y, xa.z, hi, eps2f, fx, fy, fz, fp);
     df_add(axh, axl, fx); df_add(ayh, ayl, fy); df_add(azh, azl, fz); df_add(ph_, pl, fp);
   }
   const unsigned full = 0xffffffffu, lt = (1u << lane) - 1u;
@@ -335,7 +339,7 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
 #pragma unroll 4
       for (int j = sl; j < nN; j += K) {
         const float4 s = sp[j];
-        newton32(xa.x - s.x, xa.y - s.y, xa.z - s.z, s.w, A.eps2f, fx, fy, fz, fp);
+        newton32(xa.x - s.x, xa.y - s.y, xa.z - s.z, s.w, eps2f, fx, fy, fz, fp);
       }
       if (M4) {
 #pragma unroll 1
@@ -389,6 +393,8 @@ __global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
   const bool act = sl < K;
   const int64_t it = (int64_t)fa + t;
   const double xi = A.tp.x[it], yi = A.tp.y[it], zi = A.tp.z[it], hi = A.tp.h[it];
+  const double eps = A.sys_eps[A.leaf_sys[k]];
+  const double eps2 = eps * eps;
   double fx = 0.0, fy = 0.0, fz = 0.0, fp = 0.0;
   const int64_t e0 = (int64_t)k * A.cap_near, e1 = e0 + A.near_cnt[k];
   if (act) {
@@ -399,7 +405,7 @@ __global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
         if (b == a && j == t) continue;
         const int64_t js = (int64_t)fb + j;
         pair64<SOFT>(xi - A.tp.x[js], yi - A.tp.y[js], zi - A.tp.z[js], A.tp.m[js], hi, A.tp.h[js],
-                     A.eps2, fx, fy, fz, fp);
+                     eps2, fx, fy, fz, fp);
       }
     }
   }
@@ -443,8 +449,8 @@ int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s) {
   A.lexp64 = t->lexp64;
   A.walk = t->c.walk;
   A.walk2 = t->c.walk2;
-  A.eps2 = t->p.eps * t->p.eps;
-  A.eps2f = (float)A.eps2;
+  A.leaf_sys = t->leaf_sys;
+  A.sys_eps = t->sys_eps;
   A.a = a;
   A.phi = phi;
   const unsigned g = blocks_for((int64_t)t->nleaves * 32, 256);

@@ -147,8 +147,9 @@ struct VjpArgs {
   int64_t n;
   int nleaves, ncells;
   int soft_kind;
-  double eps2;
   bool mixed;
+  const int32_t* leaf_sys;
+  const double* sys_eps;
   const int32_t* leaf_cells;
   const int32_t* leaf_rank;
   Cells c;
@@ -366,6 +367,7 @@ __global__ void k_vjp_p2p_target(VjpArgs V) {
   const int64_t pi = (int64_t)fa + t;
   const double xi = V.tp.x[pi], yi = V.tp.y[pi], zi = V.tp.z[pi], hi = V.tp.h[pi];
   const double b[3] = {V.ab[3 * pi], V.ab[3 * pi + 1], V.ab[3 * pi + 2]};
+  const double eps = V.sys_eps[V.leaf_sys[k]], eps2 = eps * eps;
   double gx = 0.0, gy = 0.0, gz = 0.0;
   const int64_t e0 = (int64_t)k * V.cap_near;
   const int nn = V.near_cnt[k];
@@ -379,7 +381,7 @@ __global__ void k_vjp_p2p_target(VjpArgs V) {
         const double d[3] = {xi - V.tp.x[pj], yi - V.tp.y[pj], zi - V.tp.z[pj]};
         const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         double f, g;
-        pair_fg(V.soft_kind, r2, V.eps2, hi, V.tp.h[pj], f, g);
+        pair_fg(V.soft_kind, r2, eps2, hi, V.tp.h[pj], f, g);
         const double db = d[0] * b[0] + d[1] * b[1] + d[2] * b[2];
         const double mj = V.tp.m[pj];
         // J b = -f b - (f'/r) d (d.b)
@@ -414,6 +416,7 @@ __global__ void k_vjp_p2p_source(VjpArgs V) {
   const bool act = sl < K;
   const int64_t pj = (int64_t)fb + j;
   const double xj = V.tp.x[pj], yj = V.tp.y[pj], zj = V.tp.z[pj], hj = V.tp.h[pj], mj = V.tp.m[pj];
+  const double eps = V.sys_eps[V.leaf_sys[k]], eps2 = eps * eps;   // near lists stay in a system
   double gx = 0.0, gy = 0.0, gz = 0.0, gm = 0.0;
   if (act) {
     for (int e = V.tr_off[k]; e < V.tr_off[k + 1]; ++e) {
@@ -426,7 +429,7 @@ __global__ void k_vjp_p2p_source(VjpArgs V) {
         const double b[3] = {V.ab[3 * pi], V.ab[3 * pi + 1], V.ab[3 * pi + 2]};
         const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         double f, g;
-        pair_fg(V.soft_kind, r2, V.eps2, V.tp.h[pi], hj, f, g);
+        pair_fg(V.soft_kind, r2, eps2, V.tp.h[pi], hj, f, g);
         const double db = d[0] * b[0] + d[1] * b[1] + d[2] * b[2];
         gx -= mj * (-f * b[0] - g * d[0] * db);
         gy -= mj * (-f * b[1] - g * d[1] * db);
@@ -548,7 +551,8 @@ int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, 
   V.nleaves = nl;
   V.ncells = nc;
   V.soft_kind = t->p.soft_kind;
-  V.eps2 = t->p.eps * t->p.eps;
+  V.leaf_sys = t->leaf_sys;
+  V.sys_eps = t->sys_eps;
   V.mixed = t->p.precision == KDFMM_MIXED;
   V.leaf_cells = t->leaf_cells;
   V.leaf_rank = t->leaf_rank;

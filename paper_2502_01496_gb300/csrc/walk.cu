@@ -31,7 +31,10 @@ struct WalkArgs {
   const int32_t* leaf_cells;
   int nleaves, ncells;
   const float* com_bound;
-  double theta, r_kern;
+  const int32_t* leaf_sys;         // system of each leaf
+  const int32_t* sys_root;         // first cell of each system (+ end)
+  const double* sys_theta;
+  double r_kern;
   int32_t *far_cnt, *near_cnt;
   int32_t *far_idx, *near_idx;     // leaf k's lists start at k * cap_far / k * cap_near
   int64_t cap_far, cap_near;
@@ -79,20 +82,23 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs W) {
   const float ha = W.walk2[a].x;
   const double ax = W.cx[a], ay = W.cy[a], az = W.cz[a], sa = W.s[a], ha64 = W.hmax[a];
   const float bound = *W.com_bound;
-  const float thf = (float)W.theta, rkf = (float)W.r_kern;
-  const bool always = W.theta == 0.0;
+  const int sys = W.leaf_sys[k];
+  const double theta = W.sys_theta[sys];
+  const int i_end = W.sys_root[sys + 1];
+  const float thf = (float)theta, rkf = (float)W.r_kern;
+  const bool always = theta == 0.0;
   int32_t* far = W.far_idx + (int64_t)k * W.cap_far;
   int32_t* near = W.near_idx + (int64_t)k * W.cap_near;
   int nf = 0, nn = 0, nex = 0;
   long long np = 0;
-  int i = 0;
-  while (i < W.ncells) {
+  int i = W.sys_root[sys];              // the walk stays inside the leaf's own tree
+  while (i < i_end) {
     const float4 wb = W.walk[i];
     const float2 w2 = W.walk2[i];
     const int skip = __float_as_int(w2.y);
     int o = always ? 1 : open_filter(wa, ha, wb, w2.x, thf, rkf, bound);
     if (o < 0) {
-      o = open_exact(ax, ay, az, sa, ha64, W.cx[i], W.cy[i], W.cz[i], W.s[i], W.hmax[i], W.theta,
+      o = open_exact(ax, ay, az, sa, ha64, W.cx[i], W.cy[i], W.cz[i], W.s[i], W.hmax[i], theta,
                      W.r_kern);
       ++nex;
     }
@@ -166,7 +172,9 @@ int run_walk(kdfmm_tree_s* t, cudaStream_t s) {
     W.nleaves = nl;
     W.ncells = t->ncells;
     W.com_bound = t->com_bound;
-    W.theta = t->p.theta;
+    W.leaf_sys = t->leaf_sys;
+    W.sys_root = t->sys_root;
+    W.sys_theta = t->sys_theta;
     W.r_kern = t->p.r_kern;
     W.far_cnt = L.far_cnt;
     W.near_cnt = L.near_cnt;

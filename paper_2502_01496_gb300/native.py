@@ -75,14 +75,17 @@ def lib() -> ctypes.CDLL:
     L.kdfmm_total_momentum_noalloc.argtypes = [P, P, i64, P, P]
     L.kdfmm_tree_stats.argtypes = [P, P]
     L.kdfmm_tree_export.argtypes = [P, P, P, P, P, P, P, P, P]
+    L.kdfmm_forest_build.argtypes = [P, P, P, P, P, i32, P, P, P, ctypes.POINTER(Params), P]
+    L.kdfmm_fmm_accel_batched.argtypes = [P, P, P, P, P, i32, P, P, P, ctypes.POINTER(Params),
+                                          P, P, P]
     L.kdfmm_tree_timing.argtypes = [P, ctypes.c_int, P]
     L.kdfmm_tree_timing.restype = i32
     L.kdfmm_last_error.restype = ctypes.c_char_p
     L.kdfmm_last_error.argtypes = []
     for name in ("kdfmm_tree_create", "kdfmm_tree_build", "kdfmm_tree_moments", "kdfmm_fmm_accel",
                  "kdfmm_fmm_accel_vjp", "kdfmm_total_momentum", "kdfmm_total_momentum_noalloc",
-                 "kdfmm_tree_stats",
-                 "kdfmm_tree_export"):
+                 "kdfmm_tree_stats", "kdfmm_tree_export", "kdfmm_forest_build",
+                 "kdfmm_fmm_accel_batched"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -140,6 +143,69 @@ def tree_build(tree, x, m, h, params: Params, stream=None) -> None:
         _dev_f64(h, "h", (n,))
     _check(lib().kdfmm_tree_build(tree, _ptr(x), _ptr(m), _ptr(h), n, ctypes.byref(params),
                                   _stream(stream)), "tree_build")
+
+
+def _host_array(a, dtype, n, name):
+    import numpy as np
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if arr.shape != (n,):
+        raise ValueError(f"{name} has shape {arr.shape}, expected ({n},)")
+    return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+def _systems(sys_offset, theta, eps, n_leaf):
+    import numpy as np
+    off = np.ascontiguousarray(sys_offset, dtype=np.int64)
+    if off.ndim != 1 or off.size < 2:
+        raise ValueError("sys_offset needs n_sys + 1 >= 2 entries")
+    n_sys = off.size - 1
+    keep = [off]
+    ptrs = [off.ctypes.data_as(ctypes.c_void_p)]
+    for a, dt, name in ((theta, np.float64, "theta"), (eps, np.float64, "eps"),
+                        (n_leaf, np.int32, "n_leaf")):
+        arr, ptr = _host_array(a, dt, n_sys, name)
+        keep.append(arr)
+        ptrs.append(ptr)
+    return n_sys, ptrs, keep
+
+
+def forest_build(tree, x, m, h, sys_offset, params: Params, theta=None, eps=None, n_leaf=None,
+                 stream=None) -> None:
+    """Builds one tree per system (particles sys_offset[k]:sys_offset[k+1])
+    in the same launches; theta / eps / n_leaf per system or None for the
+    value in params.  See include/kdfmm.h."""
+    n = x.shape[0]
+    _dev_f64(x, "x", (n, 3))
+    _dev_f64(m, "m", (n,))
+    if h is not None:
+        _dev_f64(h, "h", (n,))
+    n_sys, ptrs, keep = _systems(sys_offset, theta, eps, n_leaf)
+    if int(keep[0][-1]) != n:
+        raise ValueError(f"sys_offset ends at {int(keep[0][-1])}, x holds {n} particles")
+    _check(lib().kdfmm_forest_build(tree, _ptr(x), _ptr(m), _ptr(h), ptrs[0], n_sys, ptrs[1],
+                                    ptrs[2], ptrs[3], ctypes.byref(params), _stream(stream)),
+           "forest_build")
+
+
+def fmm_accel_batched(tree, x, m, h, sys_offset, params: Params, a, phi=None, theta=None,
+                      eps=None, n_leaf=None, stream=None) -> None:
+    """forest_build + fmm_accel in one call."""
+    n = x.shape[0]
+    _dev_f64(x, "x", (n, 3))
+    _dev_f64(m, "m", (n,))
+    if h is not None:
+        _dev_f64(h, "h", (n,))
+    _dev_f64(a, "a", (n, 3))
+    if phi is not None:
+        _dev_f64(phi, "phi", (n,))
+    n_sys, ptrs, keep = _systems(sys_offset, theta, eps, n_leaf)
+    if int(keep[0][-1]) != n:
+        raise ValueError(f"sys_offset ends at {int(keep[0][-1])}, x holds {n} particles")
+    _check(lib().kdfmm_fmm_accel_batched(tree, _ptr(x), _ptr(m), _ptr(h), ptrs[0], n_sys, ptrs[1],
+                                         ptrs[2], ptrs[3], ctypes.byref(params), _ptr(a),
+                                         _ptr(phi), _stream(stream)), "fmm_accel_batched")
 
 
 def tree_moments(tree, x, m, h, stream=None) -> None:
@@ -264,6 +330,12 @@ class KdFmm:
 
     def build(self, x, m, h=None, stream=None):
         tree_build(self.handle, x, m, h, self.params, stream)
+        self.n = x.shape[0]
+        return self
+
+    def build_forest(self, x, m, h, sys_offset, theta=None, eps=None, n_leaf=None, stream=None):
+        """Independent systems in one handle (see forest_build)."""
+        forest_build(self.handle, x, m, h, sys_offset, self.params, theta, eps, n_leaf, stream)
         self.n = x.shape[0]
         return self
 

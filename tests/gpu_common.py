@@ -81,3 +81,35 @@ def rel_errors(ga, gphi, oa, ophi, rows=None):
 
 def fsum_force(m, a):
     return np.array([math.fsum(m * a[:, k]) for k in range(3)])
+
+
+def split_forest(ex, sys_offset):
+    """The export of a forest cut into one export per system, with cell ids,
+    particle positions and caller indices made local to the system (the form
+    the oracle gives for that system alone).  System k's cells are the
+    contiguous pre-order range from its root (parent -1) to the next root."""
+    from types import SimpleNamespace
+    off = np.asarray(sys_offset, dtype=np.int64)
+    ci = ex.cell_ints
+    roots = np.nonzero(ci[:, 4] == -1)[0]
+    assert roots.size == off.size - 1, (roots.size, off.size - 1)
+    ends = np.append(roots[1:], ci.shape[0])
+    leaf_bounds = np.searchsorted(ex.leaf_ids, np.append(roots, ci.shape[0]))
+    out = []
+    for k, (r0, r1) in enumerate(zip(roots, ends)):
+        ints = ci[r0:r1].copy()
+        ints[:, 0] -= off[k]
+        for col in (2, 3, 4, 6):
+            sel = ints[:, col] >= 0
+            ints[sel, col] -= r0
+        l0, l1 = leaf_bounds[k], leaf_bounds[k + 1]
+        e = SimpleNamespace(perm=ex.perm[off[k]:off[k + 1]] - off[k], cell_ints=ints,
+                            cell_reals=ex.cell_reals[r0:r1], leaf_ids=ex.leaf_ids[l0:l1] - r0,
+                            far_off=None, far_idx=None, near_off=None, near_idx=None)
+        if ex.far_off is not None:
+            fo, no = ex.far_off[l0:l1 + 1], ex.near_off[l0:l1 + 1]
+            e.far_idx = ex.far_idx[fo[0]:fo[-1]] - r0
+            e.near_idx = ex.near_idx[no[0]:no[-1]] - r0
+            e.far_off, e.near_off = fo - fo[0], no - no[0]
+        out.append(e)
+    return out

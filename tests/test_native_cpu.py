@@ -50,3 +50,26 @@ def test_params_struct_layout_matches_header():
     from paper_2502_01496_gb300 import native
     assert ctypes.sizeof(native.Params) == 40
     assert native.Params.n_leaf.offset == 24 and native.Params.reserved.offset == 36
+
+
+def test_forest_arguments_are_checked_on_the_host(libpath):
+    """Bad system tables are refused before the handle or any device pointer
+    is looked at, so this runs without a GPU."""
+    import numpy as np
+    from paper_2502_01496_gb300 import native
+    L = native.lib()
+    p = native.make_params()
+
+    def call(off, theta=None, nleaf=None):
+        off = np.asarray(off, dtype=np.int64)
+        th = None if theta is None else np.asarray(theta, dtype=np.float64)
+        nl = None if nleaf is None else np.asarray(nleaf, dtype=np.int32)
+        ptr = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+        return L.kdfmm_forest_build(None, None, None, None, ptr(off), len(off) - 1, ptr(th), None,
+                                    ptr(nl), ctypes.byref(p), None)
+
+    assert call([0, 5, 5, 9]) == -1 and "empty" in native.last_error()
+    assert call([1, 5]) == -1 and "sys_offset[0]" in native.last_error()
+    assert call([0, 5, 9], theta=[0.5, 1.5]) == -1 and "theta[1]" in native.last_error()
+    assert call([0, 5, 9], nleaf=[16, 33]) == -1 and "n_leaf[1]" in native.last_error()
+    assert call([0, 5, 9]) == -1 and "tree is NULL" in native.last_error()
