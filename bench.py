@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
+    ap.add_argument("--batched-steps", type=int, default=5,
+                    help="steps of the 256-system batch (0 skips it)")
     return ap.parse_args()
 
 
@@ -260,6 +262,55 @@ def whole_job_rate(n_per_rank: int, steps: int, max_total_ms: float, world: int)
     return world * n_per_rank * steps / (max_total_ms / 1e3) / 1e6
 
 
+def run_batched(args, dev, flush):
+    """The batch of 256 independent Plummer systems (N log-uniform in
+    [2048, 262144], theta uniform in [0.3, 1], eps 0.01, mixed precision) as one
+    forest per step: build + walk + M2L + P2P of all systems in shared launches,
+    leaf sizes from the autotuned table (and, for comparison, 16 everywhere)."""
+    import numpy as np
+    import torch
+    from paper_2502_01496_gb300 import autotune, native
+    from paper_2502_01496_gb300 import workloads as W
+    B = W.plummer_batch(256)
+    sizes = np.array([p.n for p in B.systems])
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    x = torch.tensor(np.concatenate([p.x for p in B.systems]), device=dev)
+    m = torch.tensor(np.concatenate([p.m for p in B.systems]), device=dev)
+    a = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    f = native.KdFmm(theta=0.5, eps=0.01, n_leaf=16, soft_kind=0, precision=native.MIXED)
+    table = autotune.load()
+    out = {"workload": "plummer_batch_256", "n": n, "n_sys": 256, "unit": UNIT,
+           "tuned_table": bool(table)}
+    for label, nl in (("tuned", autotune.choose(sizes, B.theta, table)),
+                      ("leaf16", np.full(256, 16, dtype=np.int32))):
+        def step():
+            native.fmm_accel_batched(f.handle, x, m, None, off, f.params, a, phi, theta=B.theta,
+                                     eps=B.eps, n_leaf=nl)
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        l0 = f.stats()["launches"]
+        ts = []
+        for _ in range(args.batched_steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        st = f.stats()
+        ms = statistics.mean(ts)
+        out[label] = {"value": n / (ms / 1e3) / 1e6, "ms_per_step": ms,
+                      "launches_per_step": (st["launches"] - l0) / args.batched_steps,
+                      "p2p": st["np2p"], "m2l": st["nfar"], "nleaves": st["nleaves"]}
+    out["value"] = out["tuned"]["value"]
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -410,6 +461,10 @@ def run_ours(args):
                "h2d_bytes_per_step": int(n * (24 + 8 + (8 if h is not None else 0))),
                "d2h_bytes_per_step": int(n * 24 + 24), "ms_per_step": ems / args.steps}
 
+    batched = None
+    if args.batched_steps > 0:
+        batched = run_batched(args, dev, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, desc, _ = oracle_rate(ps, args, args.cpu_budget_s)
@@ -426,6 +481,7 @@ def run_ours(args):
             "fp64_gpu": fp64,
             "mixed_over_fp64": (value / world / fp64["value"]) if fp64 else None,
             "phases_ms": phase_mean,
+            "batched": batched,
             "interactions": {"p2p": st["np2p"], "m2l": st["nfar"], "nleaves": st["nleaves"],
                              "ncells": st["ncells"], "p2p_per_s": st["np2p"] / (ms_per_step / 1e3),
                              "m2l_per_s": st["nfar"] / (ms_per_step / 1e3)},

@@ -416,23 +416,26 @@ int kdfmm_tree_export(kdfmm_tree t, int64_t* perm, int64_t* cell_ints, double* c
   if (far_off || far_idx || near_off || near_idx) {
     if (!t->evaluated) return set_error(KDFMM_ERR_INVALID_ARG, "no evaluation to export lists from");
     std::vector<int32_t> fc(nl), nc(nl);
+    std::vector<int64_t> fst(nl), nst(nl);
     if ((rc = D2H(fc.data(), t->L.far_cnt, nl * sizeof(int32_t)))) return rc;
     if ((rc = D2H(nc.data(), t->L.near_cnt, nl * sizeof(int32_t)))) return rc;
+    if ((rc = D2H(fst.data(), t->L.far_off, nl * sizeof(int64_t)))) return rc;
+    if ((rc = D2H(nst.data(), t->L.near_off, nl * sizeof(int64_t)))) return rc;
     std::vector<int32_t> fs, ns;
     if (far_idx) {
-      fs.resize((size_t)(nl * t->L.cap_far));
+      fs.resize((size_t)t->L.far_cap);
       if ((rc = D2H(fs.data(), t->L.far_idx, fs.size() * sizeof(int32_t)))) return rc;
     }
     if (near_idx) {
-      ns.resize((size_t)(nl * t->L.cap_near));
+      ns.resize((size_t)t->L.near_cap);
       if ((rc = D2H(ns.data(), t->L.near_idx, ns.size() * sizeof(int32_t)))) return rc;
     }
     int64_t fo = 0, no = 0;
     for (int64_t k = 0; k < nl; ++k) {
       if (far_off) far_off[k] = fo;
       if (near_off) near_off[k] = no;
-      if (far_idx) memcpy(far_idx + fo, fs.data() + k * t->L.cap_far, fc[k] * sizeof(int32_t));
-      if (near_idx) memcpy(near_idx + no, ns.data() + k * t->L.cap_near, nc[k] * sizeof(int32_t));
+      if (far_idx) memcpy(far_idx + fo, fs.data() + fst[k], fc[k] * sizeof(int32_t));
+      if (near_idx) memcpy(near_idx + no, ns.data() + nst[k], nc[k] * sizeof(int32_t));
       fo += fc[k];
       no += nc[k];
     }

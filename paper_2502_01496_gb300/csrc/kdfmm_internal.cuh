@@ -59,14 +59,17 @@ struct Cells {
   int32_t* ready;            // bottom-up arrival counters
 };
 
-// Interaction lists: leaf k's far (M2L) list is far_idx[k * cap_far ...] with
+// Interaction lists: leaf k's far (M2L) list is far_idx[far_off[k] ...] with
 // far_cnt[k] entries, its near (P2P) list likewise; entries in ascending id.
+// Slot mode: far_off[k] = k * cap_far (fixed-size slots); exact mode: the
+// scanned counts (used when a few lists are far longer than the rest).
 struct Lists {
   int32_t *far_cnt, *near_cnt;
-  int64_t *far_off, *near_off;     // nleaves + 1, filled only for export
+  int64_t *far_off, *near_off;     // nleaves + 1
   int32_t *far_idx, *near_idx;
   int64_t far_cap, near_cap;       // allocated entries
-  int64_t cap_far, cap_near;       // slot size per leaf
+  int64_t cap_far, cap_near;       // slot size per leaf (slot mode)
+  bool exact;
   int64_t* near_np;                // device statistics of the walk (4)
 };
 

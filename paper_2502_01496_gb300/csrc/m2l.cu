@@ -101,7 +101,7 @@ struct M2LArgs {
   int nleaves;
   const int32_t* far_cnt;
   const int32_t* far_idx;
-  int64_t cap_far;
+  const int64_t* far_off;
   const float4* src32;
   const double* src64;
   float* lexp32;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_m2l_mixed(M2LArgs A) {
   for (int j = 0; j < 20; ++j) acc[j] = 0.0f;
 #pragma unroll
   for (int j = 0; j < 4; ++j) lo[j] = 0.0f;
-  const int64_t off = (int64_t)k * A.cap_far, nf = A.far_cnt[k];
+  const int64_t off = A.far_off[k], nf = A.far_cnt[k];
   for (int64_t e = lane; e < nf; e += 32) {
     const int b = A.far_idx[off + e];
     const float4 b0 = A.src32[4 * b], b1 = A.src32[4 * b + 1], b2 = A.src32[4 * b + 2],
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(256) k_m2l_fp64(M2LArgs A) {
   double acc[20];
 #pragma unroll
   for (int j = 0; j < 20; ++j) acc[j] = 0.0;
-  const int64_t off = (int64_t)k * A.cap_far, nf = A.far_cnt[k];
+  const int64_t off = A.far_off[k], nf = A.far_cnt[k];
   for (int64_t e = lane; e < nf; e += 32) {
     const int b = A.far_idx[off + e];
     const double* sb = A.src64 + 10 * (int64_t)b;
@@ -202,7 +202,7 @@ int run_m2l(kdfmm_tree_s* t, cudaStream_t s) {
   A.leaf_cells = t->leaf_cells;
   A.nleaves = t->nleaves;
   A.far_cnt = t->L.far_cnt;
-  A.cap_far = t->L.cap_far;
+  A.far_off = t->L.far_off;
   A.far_idx = t->L.far_idx;
   A.src32 = t->c.src32;
   A.src64 = t->c.src64;

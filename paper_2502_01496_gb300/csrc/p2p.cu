@@ -32,7 +32,7 @@ struct P2PArgs {
   const int32_t *cfirst, *ccount;
   const int32_t* near_cnt;
   const int32_t* near_idx;
-  int64_t cap_near;
+  const int64_t* near_off;
   const float4* src32;       // cell (hi, M), (lo, 0), ...
   const float4* pf;          // (x - com_leaf, m)
   const float4* ph;          // (1/h, 1/h^3, h, 0)
@@ -270,8 +270,8 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
     df_add(axh, axl, fx); df_add(ayh, ayl, fy); df_add(azh, azl, fz); df_add(ph_, pl, fp);
   }
   const unsigned full = 0xffffffffu, lt = (1u << lane) - 1u;
-  const int64_t e1 = (int64_t)k * A.cap_near + A.near_cnt[k];
-  for (int64_t e = (int64_t)k * A.cap_near; e < e1;) {
+  const int64_t e1 = A.near_off[k] + A.near_cnt[k];
+  for (int64_t e = A.near_off[k]; e < e1;) {
     // up to 32 candidate leaves, one per lane
     const int64_t my = e + lane;
     int cnt = 0, first = 0;
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
   const double eps = A.sys_eps[A.leaf_sys[k]];
   const double eps2 = eps * eps;
   double fx = 0.0, fy = 0.0, fz = 0.0, fp = 0.0;
-  const int64_t e0 = (int64_t)k * A.cap_near, e1 = e0 + A.near_cnt[k];
+  const int64_t e0 = A.near_off[k], e1 = e0 + A.near_cnt[k];
   if (act) {
     for (int64_t e = e0; e < e1; ++e) {
       const int b = A.near_idx[e];
@@ -438,7 +438,7 @@ int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s) {
   A.cfirst = t->c.first;
   A.ccount = t->c.count;
   A.near_cnt = t->L.near_cnt;
-  A.cap_near = t->L.cap_near;
+  A.near_off = t->L.near_off;
   A.near_idx = t->L.near_idx;
   A.src32 = t->c.src32;
   A.pf = t->pf;

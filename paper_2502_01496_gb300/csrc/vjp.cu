@@ -157,7 +157,7 @@ struct VjpArgs {
   const float* lexp32;
   const double* lexp64;
   const int32_t *far_cnt, *far_idx, *near_cnt, *near_idx;
-  int64_t cap_far, cap_near;
+  const int64_t *far_off, *near_off;
   const int32_t *tr_off, *tr_idx;       // transposed near lists (leaf ordinals)
   double* ab;                           // cotangent in tree order (N x 3)
   double* xbar;                         // tree order (N x 3)
@@ -256,7 +256,7 @@ __global__ void k_vjp_m2l(VjpArgs V) {
   for (int j = 0; j < 20; ++j) cb[j] = V.cbar[20 * (int64_t)k + j];
   const double ax = V.c.cx[a], ay = V.c.cy[a], az = V.c.cz[a];
   double rx = 0.0, ry = 0.0, rz = 0.0;
-  const int64_t off = (int64_t)k * V.cap_far;
+  const int64_t off = V.far_off[k];
   const int nf = V.far_cnt[k];
   const double zq[6] = {0, 0, 0, 0, 0, 0};
   for (int e = lane; e < nf; e += 32) {
@@ -369,7 +369,7 @@ __global__ void k_vjp_p2p_target(VjpArgs V) {
   const double b[3] = {V.ab[3 * pi], V.ab[3 * pi + 1], V.ab[3 * pi + 2]};
   const double eps = V.sys_eps[V.leaf_sys[k]], eps2 = eps * eps;
   double gx = 0.0, gy = 0.0, gz = 0.0;
-  const int64_t e0 = (int64_t)k * V.cap_near;
+  const int64_t e0 = V.near_off[k];
   const int nn = V.near_cnt[k];
   if (act) {
     for (int e = 0; e < nn; ++e) {
@@ -510,13 +510,13 @@ __global__ void k_scatter_bar(VjpArgs V, double* __restrict__ x_bar, double* __r
 __global__ void k_tr_count(VjpArgs V, int32_t* cnt) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= V.nleaves) return;
-  const int64_t e0 = (int64_t)k * V.cap_near;
+  const int64_t e0 = V.near_off[k];
   for (int e = 0; e < V.near_cnt[k]; ++e) atomicAdd(&cnt[V.leaf_rank[V.near_idx[e0 + e]]], 1);
 }
 __global__ void k_tr_fill(VjpArgs V, const int32_t* off, int32_t* cursor, int32_t* idx) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= V.nleaves) return;
-  const int64_t e0 = (int64_t)k * V.cap_near;
+  const int64_t e0 = V.near_off[k];
   for (int e = 0; e < V.near_cnt[k]; ++e) {
     const int b = V.leaf_rank[V.near_idx[e0 + e]];
     idx[off[b] + atomicAdd(&cursor[b], 1)] = k;
@@ -562,7 +562,7 @@ int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, 
   V.lexp64 = t->lexp64;
   V.far_cnt = t->L.far_cnt; V.far_idx = t->L.far_idx;
   V.near_cnt = t->L.near_cnt; V.near_idx = t->L.near_idx;
-  V.cap_far = t->L.cap_far; V.cap_near = t->L.cap_near;
+  V.far_off = t->L.far_off; V.near_off = t->L.near_off;
   double* dp = reinterpret_cast<double*>(buf);
   V.ab = dp; dp += 3 * n;
   V.xbar = dp; dp += 3 * n;

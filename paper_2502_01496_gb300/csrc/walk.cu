@@ -16,6 +16,9 @@
 // margin (about 1e-6 relative) is re-evaluated in float64 with the reference's
 // expression order and no contraction.
 #include <algorithm>
+#include <climits>
+#include <cstdlib>
+#include <cstring>
 
 #include "kdfmm_internal.cuh"
 
@@ -36,8 +39,10 @@ struct WalkArgs {
   const double* sys_theta;
   double r_kern;
   int32_t *far_cnt, *near_cnt;
-  int32_t *far_idx, *near_idx;     // leaf k's lists start at k * cap_far / k * cap_near
-  int64_t cap_far, cap_near;
+  int64_t *far_off, *near_off;     // where leaf k's lists start
+  int32_t *far_idx, *near_idx;
+  int64_t cap_far, cap_near;       // slot mode: entries per leaf (k * cap is the start)
+  bool exact;                      // exact mode: far_off / near_off are given, no limit
   int32_t* maxc;                   // [0] longest far list, [1] longest near list
   unsigned long long* stats;       // [0] P2P interactions, [1] float64 decisions, [2] far, [3] near
 };
@@ -71,9 +76,10 @@ __device__ __forceinline__ int open_filter(float4 a, float ha, float4 b, float h
   return -1;
 }
 
-// One thread per leaf, one pass: the lists go to fixed-capacity slots of the
-// leaf (entries beyond the capacity are counted, not stored; the host then
-// grows the slots and walks again).
+// One thread per leaf.  Slot mode: the lists go to fixed-capacity slots of
+// the leaf (entries beyond the capacity are counted, not stored; the host
+// then grows the slots and walks again, or switches to exact mode).  Exact
+// mode: the counts of a previous pass, scanned, give each leaf's start.
 __global__ void __launch_bounds__(128) k_walk(WalkArgs W) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= W.nleaves) return;
@@ -87,8 +93,20 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs W) {
   const int i_end = W.sys_root[sys + 1];
   const float thf = (float)theta, rkf = (float)W.r_kern;
   const bool always = theta == 0.0;
-  int32_t* far = W.far_idx + (int64_t)k * W.cap_far;
-  int32_t* near = W.near_idx + (int64_t)k * W.cap_near;
+  int64_t fo, no;
+  if (W.exact) {
+    fo = W.far_off[k];
+    no = W.near_off[k];
+  } else {
+    fo = (int64_t)k * W.cap_far;
+    no = (int64_t)k * W.cap_near;
+    W.far_off[k] = fo;
+    W.near_off[k] = no;
+  }
+  int32_t* far = W.far_idx + fo;
+  int32_t* near = W.near_idx + no;
+  const int64_t cap_far = W.exact ? INT64_MAX : W.cap_far;
+  const int64_t cap_near = W.exact ? INT64_MAX : W.cap_near;
   int nf = 0, nn = 0, nex = 0;
   long long np = 0;
   int i = W.sys_root[sys];              // the walk stays inside the leaf's own tree
@@ -104,13 +122,13 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs W) {
     }
     if (o) {
       if (skip == i + 1) {                    // opened leaf: short range
-        if (nn < W.cap_near) near[nn] = i;
+        if (nn < cap_near) near[nn] = i;
         np += W.count[i];
         ++nn;
       }
       i = i + 1;
     } else {                                  // closed: long range, skip its subtree
-      if (nf < W.cap_far) far[nf] = i;
+      if (nf < cap_far) far[nf] = i;
       ++nf;
       i = skip;
     }
@@ -130,76 +148,103 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 
 }  // namespace
 
-int ensure_lists(kdfmm_tree_s* t, int64_t cap_far, int64_t cap_near) {
-  Lists& L = t->L;
-  const int64_t nl = t->nleaves;
-  if (L.far_cap < nl * cap_far) {
-    cudaFree(L.far_idx);
-    L.far_idx = nullptr;
-    L.far_cap = 0;
-    if (cudaMalloc(&L.far_idx, nl * cap_far * sizeof(int32_t)) != cudaSuccess)
-      return set_error(KDFMM_ERR_OOM, "far list slots (%lld x %lld)", (long long)nl,
-                       (long long)cap_far);
-    L.far_cap = nl * cap_far;
-  }
-  if (L.near_cap < nl * cap_near) {
-    cudaFree(L.near_idx);
-    L.near_idx = nullptr;
-    L.near_cap = 0;
-    if (cudaMalloc(&L.near_idx, nl * cap_near * sizeof(int32_t)) != cudaSuccess)
-      return set_error(KDFMM_ERR_OOM, "near list slots (%lld x %lld)", (long long)nl,
-                       (long long)cap_near);
-    L.near_cap = nl * cap_near;
-  }
-  L.cap_far = cap_far;
-  L.cap_near = cap_near;
+static int ensure_idx(int32_t** idx, int64_t* have, int64_t need, const char* what) {
+  if (*have >= need) return KDFMM_OK;
+  cudaFree(*idx);
+  *idx = nullptr;
+  *have = 0;
+  if (cudaMalloc(idx, (size_t)std::max<int64_t>(need, 1) * sizeof(int32_t)) != cudaSuccess)
+    return set_error(KDFMM_ERR_OOM, "%s (%lld entries)", what, (long long)need);
+  *have = need;
   return KDFMM_OK;
+}
+
+// Slots waste memory when a few leaves have far longer lists than the rest
+// (small theta on a centrally condensed system): when grown slots would take
+// more than this many bytes and more than twice the bytes of the entries
+// themselves, the lists are stored exactly instead.  The environment variable
+// KDFMM_LIST_MODE=exact forces exact lists (one extra walk pass).
+constexpr int64_t kSlotBudgetBytes = int64_t(1) << 30;
+
+static bool force_exact_lists() {
+  const char* v = getenv("KDFMM_LIST_MODE");
+  return v != nullptr && strcmp(v, "exact") == 0;
 }
 
 int run_walk(kdfmm_tree_s* t, cudaStream_t s) {
   const int nl = t->nleaves;
   Lists& L = t->L;
   int64_t cf = L.cap_far > 0 ? L.cap_far : 512, cn = L.cap_near > 0 ? L.cap_near : 128;
-  for (int attempt = 0; attempt < 4; ++attempt) {
-    int rc = ensure_lists(t, cf, cn);
-    if (rc) return rc;
-    WalkArgs W{};
-    W.walk = t->c.walk;
-    W.walk2 = t->c.walk2;
-    W.cx = t->c.cx; W.cy = t->c.cy; W.cz = t->c.cz; W.s = t->c.s; W.hmax = t->c.hmax;
-    W.count = t->c.count;
-    W.leaf_cells = t->leaf_cells;
-    W.nleaves = nl;
-    W.ncells = t->ncells;
-    W.com_bound = t->com_bound;
-    W.leaf_sys = t->leaf_sys;
-    W.sys_root = t->sys_root;
-    W.sys_theta = t->sys_theta;
-    W.r_kern = t->p.r_kern;
-    W.far_cnt = L.far_cnt;
-    W.near_cnt = L.near_cnt;
+  WalkArgs W{};
+  W.walk = t->c.walk;
+  W.walk2 = t->c.walk2;
+  W.cx = t->c.cx; W.cy = t->c.cy; W.cz = t->c.cz; W.s = t->c.s; W.hmax = t->c.hmax;
+  W.count = t->c.count;
+  W.leaf_cells = t->leaf_cells;
+  W.nleaves = nl;
+  W.ncells = t->ncells;
+  W.com_bound = t->com_bound;
+  W.leaf_sys = t->leaf_sys;
+  W.sys_root = t->sys_root;
+  W.sys_theta = t->sys_theta;
+  W.r_kern = t->p.r_kern;
+  W.far_cnt = L.far_cnt;
+  W.near_cnt = L.near_cnt;
+  W.far_off = L.far_off;
+  W.near_off = L.near_off;
+  W.maxc = t->counters + 8;
+  W.stats = reinterpret_cast<unsigned long long*>(L.near_np);
+  int32_t* hc = t->host_counters;
+  int rc;
+  auto launch = [&](bool exact) {
+    W.exact = exact;
     W.far_idx = L.far_idx;
     W.near_idx = L.near_idx;
     W.cap_far = cf;
     W.cap_near = cn;
-    W.maxc = t->counters + 8;
-    W.stats = reinterpret_cast<unsigned long long*>(L.near_np);
     cudaMemsetAsync(L.near_np, 0, 4 * sizeof(int64_t), s);
     cudaMemsetAsync(t->counters + 8, 0, 2 * sizeof(int32_t), s);
     k_walk<<<blocks_for(nl, 128), 128, 0, s>>>(W);
     t->launches += 1;
-    int32_t* hc = t->host_counters;
     cudaMemcpyAsync(hc + 8, t->counters + 8, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(t->host_stats + 16, L.near_np, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    if ((rc = check_cuda(cudaStreamSynchronize(s), "walk"))) return rc;
+    return check_cuda(cudaStreamSynchronize(s), "walk");
+  };
+  const bool force_exact = force_exact_lists();
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    if ((rc = ensure_idx(&L.far_idx, &L.far_cap, (int64_t)nl * cf, "far list slots"))) return rc;
+    if ((rc = ensure_idx(&L.near_idx, &L.near_cap, (int64_t)nl * cn, "near list slots"))) return rc;
+    if ((rc = launch(false))) return rc;
     const int64_t mf = hc[8], mn = hc[9];
-    if (mf <= cf && mn <= cn) {
-      t->host_stats[KDFMM_STAT_NFAR] = t->host_stats[16 + 2];
-      t->host_stats[KDFMM_STAT_NNEAR] = t->host_stats[16 + 3];
+    const int64_t tot_far = t->host_stats[16 + 2], tot_near = t->host_stats[16 + 3];
+    if (mf <= cf && mn <= cn && !force_exact) {
+      L.cap_far = cf;
+      L.cap_near = cn;
+      L.exact = false;
+      t->host_stats[KDFMM_STAT_NFAR] = tot_far;
+      t->host_stats[KDFMM_STAT_NNEAR] = tot_near;
       return check_cuda(cudaGetLastError(), "walk launch");
     }
-    cf = std::max<int64_t>(cf, mf + mf / 4 + 16);
-    cn = std::max<int64_t>(cn, mn + mn / 4 + 16);
+    const int64_t cf2 = std::max<int64_t>(cf, mf + mf / 4 + 16);
+    const int64_t cn2 = std::max<int64_t>(cn, mn + mn / 4 + 16);
+    const int64_t slot_bytes = (int64_t)nl * (cf2 + cn2) * 4;
+    if (force_exact || (slot_bytes > kSlotBudgetBytes && slot_bytes > 8 * (tot_far + tot_near))) {
+      // exact lists from this pass's counts: one more pass fills them
+      scan_i32_to_i64(L.far_cnt, L.far_off, nl, reinterpret_cast<int64_t*>(t->scan_tmp), s);
+      scan_i32_to_i64(L.near_cnt, L.near_off, nl, reinterpret_cast<int64_t*>(t->scan_tmp), s);
+      t->launches += 6;
+      if ((rc = ensure_idx(&L.far_idx, &L.far_cap, tot_far, "far lists"))) return rc;
+      if ((rc = ensure_idx(&L.near_idx, &L.near_cap, tot_near, "near lists"))) return rc;
+      if ((rc = launch(true))) return rc;
+      if (t->host_stats[16 + 2] != tot_far || t->host_stats[16 + 3] != tot_near)
+        return set_error(KDFMM_ERR_INTERNAL, "the two walk passes disagree");
+      L.exact = true;
+      t->host_stats[KDFMM_STAT_NFAR] = tot_far;
+      t->host_stats[KDFMM_STAT_NNEAR] = tot_near;
+      return check_cuda(cudaGetLastError(), "walk launch");
+    }
+    cf = cf2;
+    cn = cn2;
   }
   return set_error(KDFMM_ERR_CAPACITY, "interaction lists kept outgrowing their slots");
 }

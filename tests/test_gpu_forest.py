@@ -143,3 +143,37 @@ def test_batch_of_256_plummer_systems(oracle):
             rows = np.nonzero(np.isfinite(oa[:, 0]))[0]
             ea, ep = rel_errors(ga[sl], gphi[sl], oa, ophi, rows)
         assert ea.max() < 2e-5 and ep.max() < 2e-5, (k, ea.max(), ep.max())
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_exact_lists_match_slots(oracle, monkeypatch, prec):
+    """Exact (compact) interaction lists, the mode taken when a few lists are
+    far longer than the rest, give the same lists and bit-identical forces as
+    fixed slots; the adjoint agrees too."""
+    import torch
+    sizes = [4096, 700, 2500]
+    systems = [W.plummer(n, W.seed_for(3, 980 + k)) for k, n in enumerate(sizes)]
+    theta = [0.3, 0.6, 1.0]
+    n_leaf = [16, 8, 32]
+    eps = [0.01] * 3
+    f1, off, ga1, gp1 = _run_forest(systems, theta, eps, n_leaf, prec, 0)
+    ex1 = f1.export(lists=True)
+    rng = np.random.default_rng(3)
+    ab = _cuda(rng.standard_normal((off[-1], 3)))
+    xb1, mb1 = f1.vjp(ab)
+    monkeypatch.setenv("KDFMM_LIST_MODE", "exact")
+    f2, _, ga2, gp2 = _run_forest(systems, theta, eps, n_leaf, prec, 0)
+    ex2 = f2.export(lists=True)
+    xb2, mb2 = f2.vjp(ab)
+    torch.cuda.synchronize()
+    for name in ("leaf_ids", "far_off", "far_idx", "near_off", "near_idx"):
+        assert np.array_equal(getattr(ex1, name), getattr(ex2, name)), name
+    assert np.array_equal(ga1, ga2) and np.array_equal(gp1, gp2)
+    xb1, xb2 = xb1.cpu().numpy(), xb2.cpu().numpy()
+    mb1, mb2 = mb1.cpu().numpy(), mb2.cpu().numpy()
+    assert np.abs(xb1 - xb2).max() <= 1e-12 * np.abs(xb1).max()
+    assert np.abs(mb1 - mb2).max() <= 1e-12 * np.abs(mb1).max()
+    parts = split_forest(ex2, off)
+    for k, ps in enumerate(systems):
+        T = oracle.Tree(ps.x, ps.m, None, theta=theta[k], n_leaf=n_leaf[k], soft_kind=0, eps=eps[k])
+        assert_lists_bit_exact({"ex": parts[k]}, {"lists": T.walk()})
