@@ -230,7 +230,21 @@ __device__ __forceinline__ void newton32(float rx, float ry, float rz, float mj,
   fp -= minv;
 }
 
+// Newtonian pair for r2 > 0 outside both kernel supports; contributes
+// nothing when `inside` (that pair is evaluated with the kernel instead).
+__device__ __forceinline__ void newton32_outside(float rx, float ry, float rz, float r2, float mj,
+                                                 bool inside, float& fx, float& fy, float& fz,
+                                                 float& fp) {
+  const float inv = rsqrtf(r2);
+  const float m1 = mj * inv;
+  const float minv = inside ? 0.0f : m1;
+  const float f = inside ? 0.0f : m1 * inv * inv;
+  fx -= f * rx; fy -= f * ry; fz -= f * rz;
+  fp -= minv;
+}
+
 constexpr int kStageCap = 256;     // staged sources per warp and chunk
+constexpr int kStageRounds = 4;    // staging loads in flight per lane (half with M4 data)
 constexpr int kP2PWarps = 4;
 
 // Mixed precision.  Per chunk of near leaves the warp stages their particles
@@ -243,13 +257,19 @@ constexpr int kP2PWarps = 4;
 template <int SOFT>
 __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
   constexpr bool M4 = SOFT == KDFMM_SOFT_M4;
+  constexpr int R = M4 ? kStageRounds / 2 : kStageRounds;
   __shared__ float4 s_pos[kP2PWarps][kStageCap];
   __shared__ float4 s_ker[M4 ? kP2PWarps : 1][M4 ? kStageCap : 1];
+  __shared__ int s_tbeg[kP2PWarps][32], s_tfirst[kP2PWarps][32];   // chunk's leaves: staged start, first
+  __shared__ float4 s_toff[kP2PWarps][32];                          // and offset to the target com
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = blockIdx.x * kP2PWarps + warp;
   if (k >= A.nleaves) return;
   float4* sp = s_pos[warp];
   float4* sk = s_ker[M4 ? warp : 0];
+  int* tb = s_tbeg[warp];
+  int* tf = s_tfirst[warp];
+  float4* toff = s_toff[warp];
   const int a = A.leaf_cells[k];
   const int fa = A.cfirst[a], nt = A.ccount[a];
   const int K = 32 / nt;
@@ -294,37 +314,54 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
       if (lane >= o) incl += w;
     }
     const int L = __popc(__ballot_sync(full, my < e1 && incl <= kStageCap));
-    // stage the chunk's sources: two leaves per pass (half-warps), 16 particles each step
+    // stage the chunk's sources with flat indexing: lane r*32 + lane of a
+    // batch of R rounds takes staged index idx, finds its leaf by
+    // binary search over the leaves' starts, and every load of the batch is
+    // issued before any is used (the loads are L2 gathers: latency-bound)
+    if (lane < L) {
+      tb[lane] = incl - cnt;
+      tf[lane] = first;
+      toff[lane] = make_float4(dx, dy, dz, 0.0f);
+    }
+    __syncwarp();
+    const int total = __shfl_sync(full, incl, L - 1);
     int nN = 0, nK = 0;
-    const int half = lane >> 4, hl = lane & 15;
-    for (int l = 0; l < L; l += 2) {
-      const int ll = min(l + half, 31);
-      int lc = __shfl_sync(full, cnt, ll);
-      if (l + half >= L) lc = 0;
-      const int lf = __shfl_sync(full, first, ll);
-      const float ldx = __shfl_sync(full, dx, ll), ldy = __shfl_sync(full, dy, ll),
-                  ldz = __shfl_sync(full, dz, ll);
-      const int cmax = max(__shfl_sync(full, lc, 0), __shfl_sync(full, lc, 16));
-      for (int j0 = 0; j0 < cmax; j0 += 16) {
-        const int j = j0 + hl;
-        const bool v = j < lc;
-        float4 p = make_float4(0.f, 0.f, 0.f, 0.f), hk = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r0 = 0; r0 < total; r0 += 32 * R) {
+      float4 pv[R], hv[R];
+      int lv[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int idx = r0 + 32 * r + lane;
+        int l = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (l + step < L && tb[l + step] <= idx) l += step;
+        lv[r] = l;
+        pv[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        hv[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < total) {
+          const int src = tf[l] + idx - tb[l];
+          pv[r] = A.pf[src];
+          if (M4) hv[r] = A.ph[src];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const bool v = r0 + 32 * r + lane < total;
+        const float4 o = toff[lv[r]];
+        float4 p = pv[r];
+        p.x += o.x; p.y += o.y; p.z += o.z;
         bool need = false;
-        if (v) {
-          p = A.pf[lf + j];
-          p.x += ldx; p.y += ldy; p.z += ldz;
-          if (M4) {
-            hk = A.ph[lf + j];
-            const float d = sqrtf(p.x * p.x + p.y * p.y + p.z * p.z);
-            need = d - sa < 2.0f * fmaxf(hmax_a, hk.z) * 1.0001f + 1e-20f;
-          }
+        if (M4 && v) {
+          const float d = sqrtf(p.x * p.x + p.y * p.y + p.z * p.z);
+          need = d - sa < 2.0f * fmaxf(hmax_a, hv[r].z) * 1.0001f + 1e-20f;
         }
         const unsigned vm = __ballot_sync(full, v), nm = __ballot_sync(full, v && need);
         if (v) {
           if (need) {
             const int pos = kStageCap - 1 - (nK + __popc(nm & lt));
             sp[pos] = p;
-            sk[pos] = hk;
+            sk[pos] = hv[r];
           } else {
             sp[nN + __popc(vm & ~nm & lt)] = p;
           }
@@ -342,10 +379,45 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
         newton32(xa.x - s.x, xa.y - s.y, xa.z - s.z, s.w, eps2f, fx, fy, fz, fp);
       }
       if (M4) {
-#pragma unroll 1
-        for (int j = kStageCap - nK + sl; j < kStageCap; j += K) {
-          const float4 s = sp[j];
-          m4pair32(xa.x - s.x, xa.y - s.y, xa.z - s.z, s.w, hi, sk[j], fx, fy, fz, fp);
+        // Two passes over the lane's pairs of the kernel segment, 128 at a
+        // time.  Pass 1: every pair as a plain 1/r^2 pair, except those
+        // inside either smoothing kernel's support (r < 2 max(h_i, h_j)),
+        // which are marked in a bit mask instead; pass 2 visits only the
+        // marked pairs with the full symmetrised M4 pair.  Only a sixth of the
+        // segment's pairs is inside, and a lane's marked pairs are dense work.
+        const float h2i = 4.0f * hi.z * hi.z;
+        const int j0 = kStageCap - nK + sl;
+        const int npair = j0 < kStageCap ? (kStageCap - j0 + K - 1) / K : 0;
+        for (int i0 = 0; i0 < npair; i0 += 128) {
+          const int nb = min(128, npair - i0);
+          const int jb = j0 + K * i0;
+          uint32_t in[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const int nbw = min(32, nb - 32 * w);
+#pragma unroll 4
+            for (int b = 0; b < nbw; ++b) {
+              const int j = jb + K * (32 * w + b);
+              const float4 s = sp[j];
+              const float hj = sk[j].z;
+              const float rx = xa.x - s.x, ry = xa.y - s.y, rz = xa.z - s.z;
+              const float r2 = rx * rx + ry * ry + rz * rz;
+              const bool inside = r2 < fmaxf(h2i, 4.0f * hj * hj);
+              in[w] |= (uint32_t)inside << b;
+              newton32_outside(rx, ry, rz, r2, s.w, inside, fx, fy, fz, fp);
+            }
+          }
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            uint32_t msk = in[w];
+            while (msk != 0u) {
+              const int b = __ffs(msk) - 1;
+              msk &= msk - 1u;
+              const int j = jb + K * (32 * w + b);
+              const float4 s = sp[j];
+              m4pair32(xa.x - s.x, xa.y - s.y, xa.z - s.z, s.w, hi, sk[j], fx, fy, fz, fp);
+            }
+          }
         }
       }
     }
