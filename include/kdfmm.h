@@ -168,13 +168,24 @@ int kdfmm_fmm_accel(kdfmm_tree t, double* a, double* phi, void* stream);
  * a_bar: N x 3 cotangent (caller order, device); x_bar: N x 3 and m_bar: N
  * outputs (device, overwritten).  Arithmetic is float64 in both precision
  * modes (mixed mode uses the evaluation's float32 expansions); cell
- * cotangents are summed with float64 atomics, so the last bits may vary run
- * to run.  Allocates its scratch (about 56 bytes per particle plus the
- * transposed near lists) with cudaMallocAsync on `stream`.  Errors:
+ * cotangents and the P2P source-side terms are summed with float64 atomics,
+ * so the last bits may vary run to run.  Allocates its scratch (88 bytes per
+ * particle, 160 per leaf, 80 per cell) with cudaMallocAsync on `stream`.  Errors:
  * KDFMM_ERR_INVALID_ARG before any evaluation or for non-device pointers,
  * KDFMM_ERR_CUDA on allocation or launch failure. */
 int kdfmm_fmm_accel_vjp(kdfmm_tree t, const double* a_bar, double* x_bar, double* m_bar,
                         void* stream);
+
+/* One kick and one drift of a kick-drift-kick leapfrog, in place:
+ * v += dt_kick * a, then x += dt_drift * v (no drift when dt_drift is 0).
+ * A step of size dt is kick(dt/2) + drift(dt), a force evaluation at the new
+ * positions, kick(dt/2); consecutive half kicks may be merged.  The paper
+ * follows the centre of mass of leapfrog runs (Sec. 4) but prints no
+ * integrator; this is the plain gravity-only one.  x, v, a: N x 3 device
+ * arrays (caller order).  Errors: KDFMM_ERR_INVALID_ARG for n outside
+ * [1, 2^30], non-finite steps or non-device pointers. */
+int kdfmm_kick_drift(double* x, double* v, const double* a, int64_t n, double dt_kick,
+                     double dt_drift, void* stream);
 
 /* out[0..2] = sum_i m_i v_i (device pointer to 3 doubles), float64 with a
  * compensated (two-sum) combination of per-block partials in a fixed order,

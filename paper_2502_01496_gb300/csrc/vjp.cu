@@ -11,7 +11,7 @@
 // Reverse order: L2P (cotangents of each leaf's expansion and of x_i, com),
 // M2L (cotangents of r = com_alpha - com_beta, M_beta, Q_beta: C is linear in M
 // and Q, its r-derivatives come from dual numbers), P2P on the target side and
-// on the source side (transposed near lists), then the moments: per cell the
+// on the source side, then the moments: per cell the
 // cotangents (M_bar, com_bar, Q_bar) give m_bar_i and x_bar_i as a quadratic
 // polynomial in x_i, summed over the leaf's chain of ancestors.
 #include <algorithm>
@@ -81,10 +81,12 @@ __device__ __forceinline__ T c3e(int a, int b, int c, const T R[3], const T u[3]
          t3 * (R[a] * Qm[b][c] + R[b] * Qm[a][c] + R[c] * Qm[a][b] + du);
 }
 
-// 20 compact coefficients C0, C1 (3), C2 (6), C3 (10) of the potential
-// Phi = -M/R - Q_jk R_j R_k / (2 R^5) and its derivatives (see m2l.cu).
+// sum_j w_j C_j over the 20 compact coefficients C0, C1 (3), C2 (6), C3 (10)
+// of the potential Phi = -M/R - Q_jk R_j R_k / (2 R^5) and its derivatives
+// (the closed forms of m2l.cu); contracting as each coefficient is formed
+// keeps one accumulator instead of twenty.
 template <class T>
-__device__ void m2l_coeffs_t(const T R[3], double M, const double Q[6], T out[20]) {
+__device__ T m2l_contract(const T R[3], double M, const double Q[6], const double w[20]) {
   const T Qm[3][3] = {{tc<T>(Q[0]), tc<T>(Q[1]), tc<T>(Q[2])},
                       {tc<T>(Q[1]), tc<T>(Q[3]), tc<T>(Q[4])},
                       {tc<T>(Q[2]), tc<T>(Q[4]), tc<T>(Q[5])}};
@@ -105,24 +107,18 @@ __device__ void m2l_coeffs_t(const T R[3], double M, const double Q[6], T out[20
   const T s2 = -(Mt * g2) - g4 * qs;
   const T s3 = -(Mt * g3) - g5 * qs;
   const T t2 = g2 * tc<T>(-1.0 / 3.0), t3 = g3 * tc<T>(-1.0 / 3.0), t4 = g4 * tc<T>(-1.0 / 3.0);
-  out[0] = -(Mt * g0) - g2 * qs;
-  for (int i = 0; i < 3; ++i) out[1 + i] = s1 * R[i] + t2 * u[i];
-  out[4] = c2e<T>(0, 0, R, u, Qm, s1, s2, t2, t3);
-  out[5] = c2e<T>(0, 1, R, u, Qm, s1, s2, t2, t3);
-  out[6] = c2e<T>(0, 2, R, u, Qm, s1, s2, t2, t3);
-  out[7] = c2e<T>(1, 1, R, u, Qm, s1, s2, t2, t3);
-  out[8] = c2e<T>(1, 2, R, u, Qm, s1, s2, t2, t3);
-  out[9] = c2e<T>(2, 2, R, u, Qm, s1, s2, t2, t3);
-  out[10] = c3e<T>(0, 0, 0, R, u, Qm, s2, s3, t3, t4);
-  out[11] = c3e<T>(0, 0, 1, R, u, Qm, s2, s3, t3, t4);
-  out[12] = c3e<T>(0, 0, 2, R, u, Qm, s2, s3, t3, t4);
-  out[13] = c3e<T>(0, 1, 1, R, u, Qm, s2, s3, t3, t4);
-  out[14] = c3e<T>(0, 1, 2, R, u, Qm, s2, s3, t3, t4);
-  out[15] = c3e<T>(0, 2, 2, R, u, Qm, s2, s3, t3, t4);
-  out[16] = c3e<T>(1, 1, 1, R, u, Qm, s2, s3, t3, t4);
-  out[17] = c3e<T>(1, 1, 2, R, u, Qm, s2, s3, t3, t4);
-  out[18] = c3e<T>(1, 2, 2, R, u, Qm, s2, s3, t3, t4);
-  out[19] = c3e<T>(2, 2, 2, R, u, Qm, s2, s3, t3, t4);
+  T acc = tc<T>(w[0]) * (-(Mt * g0) - g2 * qs);
+  for (int i = 0; i < 3; ++i) acc += tc<T>(w[1 + i]) * (s1 * R[i] + t2 * u[i]);
+  const int c2a[6] = {0, 0, 0, 1, 1, 2}, c2b[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+    acc += tc<T>(w[4 + k]) * c2e<T>(c2a[k], c2b[k], R, u, Qm, s1, s2, t2, t3);
+  const int c3a[10] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 2}, c3b[10] = {0, 0, 0, 1, 1, 2, 1, 1, 2, 2},
+            c3c[10] = {0, 1, 2, 1, 2, 2, 1, 2, 2, 2};
+#pragma unroll
+  for (int k = 0; k < 10; ++k)
+    acc += tc<T>(w[10 + k]) * c3e<T>(c3a[k], c3b[k], c3c[k], R, u, Qm, s2, s3, t3, t4);
+  return acc;
 }
 
 // index of the compact C2 entry (a, b) and C3 entry (a, b, c)
@@ -158,10 +154,11 @@ struct VjpArgs {
   const double* lexp64;
   const int32_t *far_cnt, *far_idx, *near_cnt, *near_idx;
   const int64_t *far_off, *near_off;
-  const int32_t *tr_off, *tr_idx;       // transposed near lists (leaf ordinals)
   double* ab;                           // cotangent in tree order (N x 3)
   double* xbar;                         // tree order (N x 3)
   double* mbar;                         // tree order (N)
+  double* xsrc;                         // P2P source-side part of x_bar (N x 3, atomics)
+  double* msrc;                         // P2P source-side part of m_bar (N, atomics)
   double* cbar;                         // per leaf: 20 expansion cotangents
   double* cell_bar;                     // per cell: M_bar, com_bar (3), Q_bar (6)
 };
@@ -174,7 +171,8 @@ __global__ void k_gather_abar(const double* __restrict__ abar, VjpArgs V) {
   V.ab[3 * p + 1] = abar[3 * i + 1];
   V.ab[3 * p + 2] = abar[3 * i + 2];
   V.xbar[3 * p] = V.xbar[3 * p + 1] = V.xbar[3 * p + 2] = 0.0;
-  V.mbar[p] = 0.0;
+  V.xsrc[3 * p] = V.xsrc[3 * p + 1] = V.xsrc[3 * p + 2] = 0.0;
+  V.mbar[p] = V.msrc[p] = 0.0;
 }
 
 __device__ __forceinline__ void load_coeffs(const VjpArgs& V, int k, double C[20]) {
@@ -263,27 +261,17 @@ __global__ void k_vjp_m2l(VjpArgs V) {
     const int b = V.far_idx[off + e];
     const double r[3] = {ax - V.c.cx[b], ay - V.c.cy[b], az - V.c.cz[b]};
     const double* Qb = V.c.Q + 6 * (int64_t)b;
-    // r-derivatives
-    Dual3 R[3] = {Dual3{r[0], {1.0, 0.0, 0.0}}, Dual3{r[1], {0.0, 1.0, 0.0}},
-                  Dual3{r[2], {0.0, 0.0, 1.0}}};
-    Dual3 Cd[20];
-    m2l_coeffs_t<Dual3>(R, V.c.M[b], Qb, Cd);
-    double gr[3] = {0.0, 0.0, 0.0};
-    for (int j = 0; j < 20; ++j)
-      for (int d = 0; d < 3; ++d) gr[d] += cb[j] * Cd[j].d[d];
-    // M and Q enter linearly
-    double Cu[20];
-    m2l_coeffs_t<double>(r, 1.0, zq, Cu);
-    double mbar = 0.0;
-    for (int j = 0; j < 20; ++j) mbar += cb[j] * Cu[j];
+    // r-derivatives of sum_j cb_j C_j by dual numbers; M and Q enter linearly
+    const Dual3 R[3] = {Dual3{r[0], {1.0, 0.0, 0.0}}, Dual3{r[1], {0.0, 1.0, 0.0}},
+                        Dual3{r[2], {0.0, 0.0, 1.0}}};
+    const Dual3 cr = m2l_contract<Dual3>(R, V.c.M[b], Qb, cb);
+    const double gr[3] = {cr.d[0], cr.d[1], cr.d[2]};
+    const double mbar = m2l_contract<double>(r, 1.0, zq, cb);
     double qbar[6];
-    for (int q = 0; q < 6; ++q) {
+    for (int qq = 0; qq < 6; ++qq) {
       double eq[6] = {0, 0, 0, 0, 0, 0};
-      eq[q] = 1.0;
-      m2l_coeffs_t<double>(r, 0.0, eq, Cu);
-      double s = 0.0;
-      for (int j = 0; j < 20; ++j) s += cb[j] * Cu[j];
-      qbar[q] = s;
+      eq[qq] = 1.0;
+      qbar[qq] = m2l_contract<double>(r, 0.0, eq, cb);
     }
     rx += gr[0]; ry += gr[1]; rz += gr[2];
     double* cbb = V.cell_bar + 10 * (int64_t)b;
@@ -354,9 +342,13 @@ __device__ __forceinline__ void pair_fg(int kind, double r2, double eps2, double
   g = 0.5 * gs;
 }
 
-// P2P reverse, target side: x_bar_i += sum_j m_j J(d) a_bar_i.  Warp per leaf,
-// lanes = (target, slice).
-__global__ void k_vjp_p2p_target(VjpArgs V) {
+// P2P reverse, warp per target leaf, lanes = (target, slice) as in the
+// forward: the target side x_bar_i += sum_j m_j J(d) a_bar_i stays in the
+// lane; the source side (x_bar_j -= m_j J(d) a_bar_i, m_bar_j += K(d).a_bar_i)
+// is summed over the leaf's targets by shuffles and added with one float64
+// atomic per source into separate arrays.
+__global__ void k_vjp_p2p(VjpArgs V) {
+  const unsigned full = 0xffffffffu;
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (k >= V.nleaves) return;
@@ -371,13 +363,15 @@ __global__ void k_vjp_p2p_target(VjpArgs V) {
   double gx = 0.0, gy = 0.0, gz = 0.0;
   const int64_t e0 = V.near_off[k];
   const int nn = V.near_cnt[k];
-  if (act) {
-    for (int e = 0; e < nn; ++e) {
-      const int bc = V.near_idx[e0 + e];
-      const int fb = V.c.first[bc], nb = V.c.count[bc];
-      for (int j = sl; j < nb; j += K) {
-        const int64_t pj = (int64_t)fb + j;
-        if (pj == pi) continue;
+  for (int e = 0; e < nn; ++e) {
+    const int bc = V.near_idx[e0 + e];
+    const int fb = V.c.first[bc], nb = V.c.count[bc];
+    const int iters = (nb + K - 1) / K;
+    for (int it = 0; it < iters; ++it) {
+      const int j = sl + K * it;
+      const int64_t pj = (int64_t)fb + j;
+      double sx = 0.0, sy = 0.0, sz = 0.0, sm = 0.0;
+      if (act && j < nb && pj != pi) {
         const double d[3] = {xi - V.tp.x[pj], yi - V.tp.y[pj], zi - V.tp.z[pj]};
         const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         double f, g;
@@ -385,70 +379,36 @@ __global__ void k_vjp_p2p_target(VjpArgs V) {
         const double db = d[0] * b[0] + d[1] * b[1] + d[2] * b[2];
         const double mj = V.tp.m[pj];
         // J b = -f b - (f'/r) d (d.b)
-        gx += mj * (-f * b[0] - g * d[0] * db);
-        gy += mj * (-f * b[1] - g * d[1] * db);
-        gz += mj * (-f * b[2] - g * d[2] * db);
+        const double jx = -f * b[0] - g * d[0] * db;
+        const double jy = -f * b[1] - g * d[1] * db;
+        const double jz = -f * b[2] - g * d[2] * db;
+        gx += mj * jx; gy += mj * jy; gz += mj * jz;
+        sx = -mj * jx; sy = -mj * jy; sz = -mj * jz;
+        sm = -f * db;                                          // K(d) . a_bar_i
+      }
+      for (int o = 1; o < nt; o <<= 1) {                       // over the slice's targets
+        const double ox = __shfl_down_sync(full, sx, o), oy = __shfl_down_sync(full, sy, o);
+        const double oz = __shfl_down_sync(full, sz, o), om = __shfl_down_sync(full, sm, o);
+        if (t + o < nt) { sx += ox; sy += oy; sz += oz; sm += om; }
+      }
+      if (t == 0 && act && j < nb) {
+        atomicAdd(&V.xsrc[3 * pj], sx);
+        atomicAdd(&V.xsrc[3 * pj + 1], sy);
+        atomicAdd(&V.xsrc[3 * pj + 2], sz);
+        atomicAdd(&V.msrc[pj], sm);
       }
     }
   }
   for (int s = 1; s < K; ++s) {
     const int src = t + s * nt;
-    const double ox = __shfl_sync(0xffffffffu, gx, src), oy = __shfl_sync(0xffffffffu, gy, src),
-                 oz = __shfl_sync(0xffffffffu, gz, src);
+    const double ox = __shfl_sync(full, gx, src), oy = __shfl_sync(full, gy, src),
+                 oz = __shfl_sync(full, gz, src);
     if (sl == 0) { gx += ox; gy += oy; gz += oz; }
   }
   if (act && sl == 0) {
     V.xbar[3 * pi] += gx;
     V.xbar[3 * pi + 1] += gy;
     V.xbar[3 * pi + 2] += gz;
-  }
-}
-
-// P2P reverse, source side: for source j, over the targets i whose near list
-// holds j's leaf: x_bar_j -= m_j J(d) a_bar_i, m_bar_j += K(d) . a_bar_i.
-__global__ void k_vjp_p2p_source(VjpArgs V) {
-  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // source leaf ordinal
-  const int lane = threadIdx.x & 31;
-  if (k >= V.nleaves) return;
-  const int bcell = V.leaf_cells[k];
-  const int fb = V.c.first[bcell], ns = V.c.count[bcell];
-  const int K = 32 / ns, j = lane % ns, sl = lane / ns;
-  const bool act = sl < K;
-  const int64_t pj = (int64_t)fb + j;
-  const double xj = V.tp.x[pj], yj = V.tp.y[pj], zj = V.tp.z[pj], hj = V.tp.h[pj], mj = V.tp.m[pj];
-  const double eps = V.sys_eps[V.leaf_sys[k]], eps2 = eps * eps;   // near lists stay in a system
-  double gx = 0.0, gy = 0.0, gz = 0.0, gm = 0.0;
-  if (act) {
-    for (int e = V.tr_off[k]; e < V.tr_off[k + 1]; ++e) {
-      const int acell = V.leaf_cells[V.tr_idx[e]];
-      const int fa = V.c.first[acell], nt = V.c.count[acell];
-      for (int i = sl; i < nt; i += K) {
-        const int64_t pi = (int64_t)fa + i;
-        if (pi == pj) continue;
-        const double d[3] = {V.tp.x[pi] - xj, V.tp.y[pi] - yj, V.tp.z[pi] - zj};
-        const double b[3] = {V.ab[3 * pi], V.ab[3 * pi + 1], V.ab[3 * pi + 2]};
-        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        double f, g;
-        pair_fg(V.soft_kind, r2, eps2, V.tp.h[pi], hj, f, g);
-        const double db = d[0] * b[0] + d[1] * b[1] + d[2] * b[2];
-        gx -= mj * (-f * b[0] - g * d[0] * db);
-        gy -= mj * (-f * b[1] - g * d[1] * db);
-        gz -= mj * (-f * b[2] - g * d[2] * db);
-        gm += -f * db;                                       // K(d) . b
-      }
-    }
-  }
-  for (int s = 1; s < K; ++s) {
-    const int src = j + s * ns;
-    const double ox = __shfl_sync(0xffffffffu, gx, src), oy = __shfl_sync(0xffffffffu, gy, src),
-                 oz = __shfl_sync(0xffffffffu, gz, src), om = __shfl_sync(0xffffffffu, gm, src);
-    if (sl == 0) { gx += ox; gy += oy; gz += oz; gm += om; }
-  }
-  if (act && sl == 0) {
-    V.xbar[3 * pj] += gx;
-    V.xbar[3 * pj + 1] += gy;
-    V.xbar[3 * pj + 2] += gz;
-    V.mbar[pj] += gm;
   }
 }
 
@@ -500,38 +460,10 @@ __global__ void k_scatter_bar(VjpArgs V, double* __restrict__ x_bar, double* __r
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= V.n) return;
   const int64_t i = V.tp.idx[p];
-  x_bar[3 * i] = V.xbar[3 * p];
-  x_bar[3 * i + 1] = V.xbar[3 * p + 1];
-  x_bar[3 * i + 2] = V.xbar[3 * p + 2];
-  m_bar[i] = V.mbar[p];
-}
-
-// Transposed near lists: count, offsets, fill, then each leaf's list sorted.
-__global__ void k_tr_count(VjpArgs V, int32_t* cnt) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= V.nleaves) return;
-  const int64_t e0 = V.near_off[k];
-  for (int e = 0; e < V.near_cnt[k]; ++e) atomicAdd(&cnt[V.leaf_rank[V.near_idx[e0 + e]]], 1);
-}
-__global__ void k_tr_fill(VjpArgs V, const int32_t* off, int32_t* cursor, int32_t* idx) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= V.nleaves) return;
-  const int64_t e0 = V.near_off[k];
-  for (int e = 0; e < V.near_cnt[k]; ++e) {
-    const int b = V.leaf_rank[V.near_idx[e0 + e]];
-    idx[off[b] + atomicAdd(&cursor[b], 1)] = k;
-  }
-}
-__global__ void k_tr_sort(const int32_t* off, int32_t* idx, int nleaves) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nleaves) return;
-  const int lo = off[k], hi = off[k + 1];
-  for (int i = lo + 1; i < hi; ++i) {                 // insertion sort (short lists)
-    const int v = idx[i];
-    int j = i - 1;
-    while (j >= lo && idx[j] > v) { idx[j + 1] = idx[j]; --j; }
-    idx[j + 1] = v;
-  }
+  x_bar[3 * i] = V.xbar[3 * p] + V.xsrc[3 * p];
+  x_bar[3 * i + 1] = V.xbar[3 * p + 1] + V.xsrc[3 * p + 1];
+  x_bar[3 * i + 2] = V.xbar[3 * p + 2] + V.xsrc[3 * p + 2];
+  m_bar[i] = V.mbar[p] + V.msrc[p];
 }
 
 }  // namespace
@@ -539,10 +471,10 @@ __global__ void k_tr_sort(const int32_t* off, int32_t* idx, int nleaves) {
 int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, cudaStream_t s) {
   const int64_t n = t->n;
   const int nl = t->nleaves, nc = t->ncells;
-  // scratch: a_bar, x_bar, m_bar in tree order, expansion and cell cotangents, transposed lists
-  const int64_t nnear = t->host_stats[KDFMM_STAT_NNEAR];
-  const size_t bytes = (size_t)n * 7 * sizeof(double) + (size_t)nl * 20 * sizeof(double) +
-                       (size_t)nc * 10 * sizeof(double) + (size_t)(3 * (nl + 2) + nnear + 16) * sizeof(int32_t);
+  // scratch: a_bar, x_bar (two parts), m_bar (two parts) in tree order, then
+  // the leaves' expansion cotangents and the cells' moment cotangents
+  const size_t bytes = (size_t)n * 11 * sizeof(double) + (size_t)nl * 20 * sizeof(double) +
+                       (size_t)nc * 10 * sizeof(double);
   char* buf = nullptr;
   int rc = check_cuda(cudaMallocAsync((void**)&buf, bytes, s), "adjoint scratch");
   if (rc) return rc;
@@ -566,31 +498,19 @@ int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, 
   double* dp = reinterpret_cast<double*>(buf);
   V.ab = dp; dp += 3 * n;
   V.xbar = dp; dp += 3 * n;
+  V.xsrc = dp; dp += 3 * n;
   V.mbar = dp; dp += n;
+  V.msrc = dp; dp += n;
   V.cbar = dp; dp += 20 * (int64_t)nl;
-  V.cell_bar = dp; dp += 10 * (int64_t)nc;
-  int32_t* ip = reinterpret_cast<int32_t*>(dp);
-  int32_t* tcnt = ip; ip += nl + 2;
-  int32_t* toff = ip; ip += nl + 2;
-  int32_t* tcur = ip; ip += nl + 2;
-  int32_t* tidx = ip;
-  V.tr_off = toff;
-  V.tr_idx = tidx;
+  V.cell_bar = dp;
   cudaMemsetAsync(V.cell_bar, 0, (size_t)nc * 10 * sizeof(double), s);
-  cudaMemsetAsync(tcnt, 0, (size_t)(nl + 2) * sizeof(int32_t), s);
-  cudaMemsetAsync(tcur, 0, (size_t)(nl + 2) * sizeof(int32_t), s);
   k_gather_abar<<<blocks_for(n, 256), 256, 0, s>>>(a_bar, V);
-  k_tr_count<<<blocks_for(nl, 128), 128, 0, s>>>(V, tcnt);
-  scan_i32(tcnt, toff, nl, t->scan_tmp, s);
-  k_tr_fill<<<blocks_for(nl, 128), 128, 0, s>>>(V, toff, tcur, tidx);
-  k_tr_sort<<<blocks_for(nl, 128), 128, 0, s>>>(toff, tidx, nl);
   k_vjp_l2p<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
   k_vjp_m2l<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
-  k_vjp_p2p_target<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
-  k_vjp_p2p_source<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
+  k_vjp_p2p<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
   k_vjp_moments<<<blocks_for(nl, 128), 128, 0, s>>>(V);
   k_scatter_bar<<<blocks_for(n, 256), 256, 0, s>>>(V, x_bar, m_bar);
-  t->launches += 13;
+  t->launches += 6;
   rc = check_cuda(cudaGetLastError(), "adjoint launch");
   cudaFreeAsync(buf, s);
   return rc;

@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
     L.kdfmm_forest_build.argtypes = [P, P, P, P, P, i32, P, P, P, ctypes.POINTER(Params), P]
     L.kdfmm_fmm_accel_batched.argtypes = [P, P, P, P, P, i32, P, P, P, ctypes.POINTER(Params),
                                           P, P, P]
+    L.kdfmm_kick_drift.argtypes = [P, P, P, i64, ctypes.c_double, ctypes.c_double, P]
     L.kdfmm_tree_timing.argtypes = [P, ctypes.c_int, P]
     L.kdfmm_tree_timing.restype = i32
     L.kdfmm_last_error.restype = ctypes.c_char_p
@@ -85,7 +86,7 @@ def lib() -> ctypes.CDLL:
     for name in ("kdfmm_tree_create", "kdfmm_tree_build", "kdfmm_tree_moments", "kdfmm_fmm_accel",
                  "kdfmm_fmm_accel_vjp", "kdfmm_total_momentum", "kdfmm_total_momentum_noalloc",
                  "kdfmm_tree_stats", "kdfmm_tree_export", "kdfmm_forest_build",
-                 "kdfmm_fmm_accel_batched"):
+                 "kdfmm_fmm_accel_batched", "kdfmm_kick_drift"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -256,6 +257,16 @@ def total_momentum_noalloc(m, v, out, stream=None) -> None:
     _dev_f64(out, "out", (3,))
     _check(lib().kdfmm_total_momentum_noalloc(_ptr(m), _ptr(v), n, _ptr(out), _stream(stream)),
            "total_momentum_noalloc")
+
+
+def kick_drift(x, v, a, dt_kick: float, dt_drift: float, stream=None) -> None:
+    """v += dt_kick a; x += dt_drift v (in place, leapfrog)."""
+    n = x.shape[0]
+    _dev_f64(x, "x", (n, 3))
+    _dev_f64(v, "v", (n, 3))
+    _dev_f64(a, "a", (n, 3))
+    _check(lib().kdfmm_kick_drift(_ptr(x), _ptr(v), _ptr(a), n, float(dt_kick), float(dt_drift),
+                                  _stream(stream)), "kick_drift")
 
 
 def tree_stats(tree) -> dict:
