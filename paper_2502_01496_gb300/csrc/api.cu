@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -89,6 +90,11 @@ static int grow_eval_buffers(kdfmm_tree_s* t, int64_t cap) {
       cudaMalloc(&L.far_off, (cap + 2) * sizeof(int64_t)) != cudaSuccess ||
       cudaMalloc(&L.near_off, (cap + 2) * sizeof(int64_t)) != cudaSuccess)
     return set_error(KDFMM_ERR_OOM, "interaction list offsets");
+  // leaves that a walk skipped keep empty lists
+  cudaMemset(L.far_cnt, 0, (cap + 1) * sizeof(int32_t));
+  cudaMemset(L.near_cnt, 0, (cap + 1) * sizeof(int32_t));
+  cudaMemset(L.far_off, 0, (cap + 2) * sizeof(int64_t));
+  cudaMemset(L.near_off, 0, (cap + 2) * sizeof(int64_t));
   return KDFMM_OK;
 }
 
@@ -181,8 +187,9 @@ static int build_common(kdfmm_tree_s* t, const double* x, const double* m, const
   const int64_t old_cap = t->cap_n;
   int rc;
   phase_begin(t, KDFMM_PHASE_BUILD, s);
-  if ((rc = build_tree(t, x, m, h, s))) return rc;
+  if ((rc = build_tree(t, x, m, h, s, 0))) return rc;
   phase_end(t, KDFMM_PHASE_BUILD, s);
+  t->grid_leaves = t->nleaves;
   if (t->cap_n != old_cap || t->L.far_cnt == nullptr)
     if ((rc = grow_eval_buffers(t, t->cap_n))) return rc;
   t->built = true;
@@ -195,6 +202,130 @@ static int build_common(kdfmm_tree_s* t, const double* x, const double* m, const
   hs[KDFMM_STAT_NFALLBACK] = t->nfallback;
   hs[KDFMM_STAT_NEXACT] = 0;
   return KDFMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Captured evaluation.  The first kdfmm_fmm_accel_batched call for a set of
+// buffers runs eagerly (the host follows the device counters); its sizes,
+// with margins, fix a sequence of launches that needs no host decision
+// (phase-A levels, list slots, leaves), which is captured into a CUDA graph
+// on a private stream.  Later calls with the same buffers replay the graph
+// and read the counters once; a replay whose tree needed more levels, more
+// leaves or longer lists than the graph allows is redone eagerly and the
+// graph captured again.  KDFMM_GRAPH=0 in the environment turns this off.
+// ---------------------------------------------------------------------------
+static bool graphs_enabled() {
+  const char* v = getenv("KDFMM_GRAPH");
+  return !(v != nullptr && strcmp(v, "0") == 0);
+}
+
+static void graph_drop(kdfmm_tree_s* t) {
+  if (t->graph_exec) cudaGraphExecDestroy(t->graph_exec);
+  t->graph_exec = nullptr;
+}
+
+static kdfmm_tree_s::GraphKey graph_key_of(const kdfmm_tree_s* t, const double* x, const double* m,
+                                           const double* h, double* a, double* phi) {
+  kdfmm_tree_s::GraphKey k{};
+  k.x = x; k.m = m; k.h = h; k.a = a; k.phi = phi;
+  k.n = t->n; k.cap_n = t->cap_n;
+  k.cap_far = t->L.cap_far; k.cap_near = t->L.cap_near;
+  k.far_cap = t->L.far_cap; k.near_cap = t->L.near_cap;
+  k.n_sys = t->n_sys; k.cap_sys = t->cap_sys; k.min_nleaf = t->min_nleaf;
+  k.soft_kind = t->p.soft_kind; k.precision = t->p.precision; k.r_kern = t->p.r_kern;
+  return k;
+}
+
+// Build (fixed levels), walk (fixed slots), M2L and P2P, with no
+// synchronisation and no allocation.
+static int enqueue_fixed(kdfmm_tree_s* t, const double* x, const double* m, const double* h,
+                         double* a, double* phi, cudaStream_t s) {
+  int rc = build_tree(t, x, m, h, s, t->graph_levels);
+  if (rc) return rc;
+  t->grid_leaves = t->graph_leaves;
+  if ((rc = walk_fixed(t, t->graph_leaves, s))) return rc;
+  if ((rc = run_m2l(t, s))) return rc;
+  return run_p2p(t, a, phi, s);
+}
+
+// Captures the fixed sequence sized from the eager evaluation just done.
+// A capture that fails leaves the handle without a graph (eager calls).
+static void graph_capture(kdfmm_tree_s* t, const double* x, const double* m, const double* h,
+                          double* a, double* phi, cudaStream_t s) {
+  graph_drop(t);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {   // the lists may be copied to larger slots
+    cudaGetLastError();
+    return;
+  }
+  if (t->L.exact) return;                 // exact lists need the host between two walks
+  if (!t->capture_stream &&
+      cudaStreamCreateWithFlags(&t->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  t->graph_levels = t->levels_used + 2;
+  t->graph_leaves = (int32_t)std::min<int64_t>(t->n, (int64_t)t->nleaves + t->nleaves / 4 + 64);
+  if (ensure_slots(t, t->graph_leaves)) return;
+  const int32_t grid_eager = t->grid_leaves;
+  const int64_t launches0 = t->launches;
+  const bool timing = t->timing;
+  t->timing = false;
+  cudaStream_t cs = t->capture_stream;
+  cudaGraph_t g = nullptr;
+  int rc = KDFMM_OK;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    rc = enqueue_fixed(t, x, m, h, a, phi, cs);
+    if (cudaStreamEndCapture(cs, &g) != cudaSuccess) rc = KDFMM_ERR_CUDA;
+  } else {
+    rc = KDFMM_ERR_CUDA;
+  }
+  if (rc == KDFMM_OK && g != nullptr &&
+      cudaGraphInstantiate(&t->graph_exec, g, 0) == cudaSuccess) {
+    t->graph_key = graph_key_of(t, x, m, h, a, phi);
+    t->graph_launches = t->launches - launches0;
+  } else {
+    t->graph_exec = nullptr;
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  t->launches = launches0;                // captured launches have not run
+  t->grid_leaves = grid_eager;
+  t->timing = timing;
+}
+
+// Replays the graph; 0: done, 1: the tree outgrew the graph (redo eagerly),
+// < 0: error.
+static int graph_replay(kdfmm_tree_s* t, cudaStream_t s) {
+  int rc = check_cuda(cudaGraphLaunch(t->graph_exec, s), "graph launch");
+  if (rc) return rc;
+  t->launches += t->graph_launches;
+  int32_t* hc = t->host_counters;
+  cudaMemcpyAsync(hc, t->counters, 32 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&hc[32], t->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(t->host_stats + 16, t->L.near_np, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if ((rc = check_cuda(cudaStreamSynchronize(s), "graph replay"))) return rc;
+  const int32_t st = hc[32];
+  t->built = t->evaluated = t->lists_frozen = false;
+  if (st & ST_NONFINITE)
+    return set_error(KDFMM_ERR_NONFINITE, "non-finite position or non-positive mass / h");
+  if ((st & (ST_UNFINISHED | ST_LISTS | ST_CAPACITY | ST_INTERNAL)) ||
+      hc[C_MAXFAR] > t->L.cap_far || hc[C_MAXNEAR] > t->L.cap_near)
+    return 1;
+  t->ncells = hc[C_CELLS];
+  t->nleaves = hc[C_LEAVES];
+  t->depth = hc[C_DEPTH];
+  t->nfallback = hc[C_FALLBACK];
+  t->grid_leaves = t->graph_leaves;
+  t->built = t->evaluated = true;
+  int64_t* hs = t->host_stats;
+  hs[KDFMM_STAT_N] = t->n;
+  hs[KDFMM_STAT_NCELLS] = t->ncells;
+  hs[KDFMM_STAT_NLEAVES] = t->nleaves;
+  hs[KDFMM_STAT_DEPTH] = t->depth;
+  hs[KDFMM_STAT_NFALLBACK] = t->nfallback;
+  hs[KDFMM_STAT_NFAR] = hs[16 + 2];
+  hs[KDFMM_STAT_NNEAR] = hs[16 + 3];
+  return 0;
 }
 
 }  // namespace kdfmm
@@ -240,6 +371,8 @@ void kdfmm_tree_destroy(kdfmm_tree t) {
   cudaFree(t->sys_off); cudaFree(t->sys_theta); cudaFree(t->sys_eps); cudaFree(t->sys_nleaf);
   cudaFree(t->sys_root);
   if (t->host_sys_off) cudaFreeHost(t->host_sys_off);
+  graph_drop(t);
+  if (t->capture_stream) cudaStreamDestroy(t->capture_stream);
   for (cudaEvent_t& e : t->ev)
     if (e) cudaEventDestroy(e);
   if (t->host_stats) cudaFreeHost(t->host_stats);
@@ -290,9 +423,33 @@ int kdfmm_fmm_accel_batched(kdfmm_tree t, const double* x, const double* m, cons
                             const int64_t* sys_offset, int32_t n_sys, const double* theta,
                             const double* eps, const int32_t* n_leaf, const kdfmm_params* p,
                             double* a, double* phi, void* stream) {
-  int rc = kdfmm_forest_build(t, x, m, h, sys_offset, n_sys, theta, eps, n_leaf, p, stream);
+  int rc = check_params(p, h);
   if (rc) return rc;
-  return kdfmm_fmm_accel(t, a, phi, stream);
+  if ((rc = check_systems(sys_offset, n_sys, theta, eps, n_leaf))) return rc;
+  if (!t) return set_error(KDFMM_ERR_INVALID_ARG, "tree is NULL");
+  if (!is_device_ptr(x) || !is_device_ptr(m) || (h != nullptr && !is_device_ptr(h)) ||
+      !is_device_ptr(a) || (phi != nullptr && !is_device_ptr(phi)))
+    return set_error(KDFMM_ERR_INVALID_ARG, "x, m, a (and h, phi) must be device pointers");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return set_error(KDFMM_ERR_INVALID_ARG, "handle belongs to device %d", t->device);
+  const bool graphs = graphs_enabled();
+  if (graphs && t->graph_exec) {
+    if ((rc = set_systems(t, sys_offset, n_sys, theta, eps, n_leaf, p, s))) return rc;
+    t->n = sys_offset[n_sys];
+    t->p = *p;
+    if (graph_key_of(t, x, m, h, a, phi) == t->graph_key) {
+      rc = graph_replay(t, s);
+      if (rc <= 0) return rc;
+    }
+    graph_drop(t);                       // outgrown or other buffers: eager, then capture again
+  }
+  if ((rc = kdfmm_forest_build(t, x, m, h, sys_offset, n_sys, theta, eps, n_leaf, p, stream)))
+    return rc;
+  if ((rc = kdfmm_fmm_accel(t, a, phi, stream))) return rc;
+  if (graphs) graph_capture(t, x, m, h, a, phi, s);
+  return KDFMM_OK;
 }
 
 int kdfmm_tree_moments(kdfmm_tree t, const double* x, const double* m, const double* h,

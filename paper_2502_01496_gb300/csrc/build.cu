@@ -103,9 +103,28 @@ __device__ void push_child(const BuildArgs& A, Seg c, Seg* nextA, Seg* segB, Seg
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int nchunks_of(int count) { return (count + kChunk - 1) / kChunk; }
 
+// Start of a phase-A level: the segments pushed by the previous level are
+// this level's (counters[C_NA]); the push counter restarts.
+__global__ void k_level_begin(int32_t* counters, int64_t capA, int32_t* status) {
+  int na = counters[C_NEXT_A];
+  if (na > capA) {
+    set_status(status, ST_CAPACITY);
+    na = (int)capA;
+  }
+  counters[C_NA] = na;
+  counters[C_NEXT_A] = 0;
+}
+
+// After the last phase-A level: segments still waiting for a split mean the
+// fixed number of levels was too small.
+__global__ void k_levels_done(const int32_t* counters, int32_t* status) {
+  if (counters[C_NEXT_A] > 0) set_status(status, ST_UNFINISHED);
+}
+
 // Chunk offsets of the nA segments (single block) and the chunk -> segment map.
-__global__ void k_chunk_map(const Seg* __restrict__ segs, int nA, int32_t* __restrict__ seg_off,
+__global__ void k_chunk_map(const Seg* __restrict__ segs, const int32_t* __restrict__ nA_dev, int32_t* __restrict__ seg_off,
                             int32_t* __restrict__ chunk_seg, int32_t* counters) {
+  const int nA = *nA_dev;
   __shared__ int32_t warp_tot[32];
   __shared__ int32_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -194,10 +213,11 @@ k_chunk_reduce(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_s
 }
 
 // Warp per segment: pairwise tree over its chunk sums, centre of mass, axis, cut.
-__global__ void k_decide(const Seg* __restrict__ segs, int nA, const int32_t* __restrict__ seg_off,
+__global__ void k_decide(const Seg* __restrict__ segs, const int32_t* __restrict__ nA_dev, const int32_t* __restrict__ seg_off,
                          const double* __restrict__ csum, const long long* __restrict__ ckey,
                          TmpCells tmp, int32_t* __restrict__ seg_axis, double* __restrict__ seg_cut,
                          float* __restrict__ seg_xb, long long* __restrict__ seg_s2) {
+  const int nA = *nA_dev;
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (s >= nA) return;
@@ -304,11 +324,12 @@ k_chunk_count(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_se
 
 // Warp per segment: offsets of the left particles per chunk, the split point,
 // s, and the two children.
-__global__ void k_split(const Seg* __restrict__ segs, int nA, const int32_t* __restrict__ seg_off,
+__global__ void k_split(const Seg* __restrict__ segs, const int32_t* __restrict__ nA_dev, const int32_t* __restrict__ seg_off,
                         const int32_t* __restrict__ cleft, const float* __restrict__ cs2,
                         int32_t* __restrict__ cloff, int32_t* __restrict__ seg_nl,
                         const float* __restrict__ seg_xb, float* __restrict__ seg_thr2, BuildArgs A,
                         Seg* nextA, Seg* segB, Seg* segL, int dst_buf) {
+  const int nA = *nA_dev;
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (s >= nA) return;
@@ -421,8 +442,9 @@ k_chunk_scatter(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_
 }
 
 // Size of each phase-A cell from the exact squared maximum of its candidates.
-__global__ void k_seg_size(const Seg* __restrict__ segs, int nA, const long long* __restrict__ seg_s2,
+__global__ void k_seg_size(const Seg* __restrict__ segs, const int32_t* __restrict__ nA_dev, const long long* __restrict__ seg_s2,
                            TmpCells tmp) {
+  const int nA = *nA_dev;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < nA) tmp.s[segs[s].cell] = sqrt(__longlong_as_double(seg_s2[s]));
 }
@@ -896,7 +918,15 @@ k_subtree(SubArgs S) {
   int4* leaves = L.q[1] + S.qcap;
   const int leafcap = 2 * S.qcap;
 
-  const Seg g = S.segB[blockIdx.x];
+  // persistent: the CTA takes segments from a work counter until none is left
+  __shared__ int s_seg;
+  const int nB = min(S.A.counters[C_NB], (int)S.A.capB);
+  for (;;) {
+  __syncthreads();
+  if (threadIdx.x == 0) s_seg = atomicAdd(&S.A.counters[C_WORK], 1);
+  __syncthreads();
+  if (s_seg >= nB) break;
+  const Seg g = S.segB[s_seg];
   const PCols in = (g.dbuf & 1) ? S.buf1 : S.buf0;
   const int n = g.count;
   const int gfirst = g.first;
@@ -960,13 +990,14 @@ k_subtree(SubArgs S) {
     S.out.h[p] = in.h[gfirst + src];
     S.out.idx[p] = in.idx[gfirst + src];
   }
+  }
 }
 
 // Leaves produced directly by phase A (or a root that is already a leaf): one
 // thread per leaf, pairwise sums by a carry stack.
-__global__ void k_leaf_segs(SubArgs S, const Seg* __restrict__ segL, int nL) {
-  const int sidx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (sidx >= nL) return;
+__global__ void k_leaf_segs(SubArgs S, const Seg* __restrict__ segL) {
+  const int nL = min(S.A.counters[C_NL], (int)S.A.capL);
+  KD_GRID_STRIDE(sidx, nL) {
   const Seg g = segL[sidx];
   const PCols in = (g.dbuf & 1) ? S.buf1 : S.buf0;
   const int cnt = g.count;
@@ -999,6 +1030,7 @@ __global__ void k_leaf_segs(SubArgs S, const Seg* __restrict__ segL, int nL) {
   t.M[c] = M; t.cx[c] = cx; t.cy[c] = cy; t.cz[c] = cz;
   t.s[c] = sqrt(__longlong_as_double(s2));
   t.left[c] = -1; t.right[c] = -1;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1010,12 +1042,14 @@ __global__ void k_fill2(int32_t* a, int32_t va, int32_t* b, int32_t vb, int64_t 
   if (i < n) { a[i] = va; b[i] = vb; }
 }
 
-__global__ void k_count_starts(TmpCells tmp, int ncells, int32_t* cnt_start, int32_t* min_depth) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncells) return;
-  int f = tmp.first[c];
-  atomicAdd(&cnt_start[f], 1);
-  atomicMin(&min_depth[f], tmp.depth[c]);
+__global__ void k_count_starts(TmpCells tmp, const int32_t* __restrict__ counters,
+                               int32_t* cnt_start, int32_t* min_depth) {
+  const int ncells = counters[C_CELLS];
+  KD_GRID_STRIDE(c, ncells) {
+    const int f = tmp.first[c];
+    atomicAdd(&cnt_start[f], 1);
+    atomicMin(&min_depth[f], tmp.depth[c]);
+  }
 }
 
 __device__ __forceinline__ int preorder_id(const int32_t* start_off, const int32_t* min_depth,
@@ -1023,10 +1057,10 @@ __device__ __forceinline__ int preorder_id(const int32_t* start_off, const int32
   return start_off[first] + depth - min_depth[first];
 }
 
-__global__ void k_remap(TmpCells tmp, int ncells, const int32_t* __restrict__ start_off,
+__global__ void k_remap(TmpCells tmp, const int32_t* __restrict__ counters, const int32_t* __restrict__ start_off,
                         const int32_t* __restrict__ min_depth, Cells c, int32_t* status) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ncells) return;
+  const int t_n = counters[C_CELLS];
+  KD_GRID_STRIDE(t, t_n) {
   const int f = tmp.first[t], cnt = tmp.count[t], d = tmp.depth[t];
   const int id = preorder_id(start_off, min_depth, f, d);
   c.first[id] = f; c.count[id] = cnt; c.depth[id] = d;
@@ -1045,6 +1079,7 @@ __global__ void k_remap(TmpCells tmp, int ncells, const int32_t* __restrict__ st
     c.left[id] = -1; c.right[id] = -1;
   }
   if (d == 0) c.parent[id] = -1;               // a system's root
+  }
 }
 
 // Pre-order id of each system's root; sys_root[n_sys] = number of cells.
@@ -1057,9 +1092,9 @@ __global__ void k_sys_roots(const int64_t* __restrict__ sys_off, int n_sys,
 // Leaves: h_max and Q (Eq. 7) from their particles (one thread per leaf);
 // then each parent, once its second child has finished, from its children
 // (parallel-axis shift of Q).  Every sum runs in a fixed order.
-__global__ void k_upward(Cells c, const int32_t* __restrict__ leaf_cells, int nleaves, PCols tp) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nleaves) return;
+__global__ void k_upward(Cells c, const int32_t* __restrict__ leaf_cells, const int32_t* __restrict__ counters, PCols tp) {
+  const int k_n = counters[C_LEAVES];
+  KD_GRID_STRIDE(k, k_n) {
   const int t = leaf_cells[k];
   double q[6] = {0, 0, 0, 0, 0, 0}, hm = 0.0;
   {
@@ -1108,17 +1143,18 @@ __global__ void k_upward(Cells c, const int32_t* __restrict__ leaf_cells, int nl
     c.hmax[p] = hp;
     cur = p;
   }
+  }
 }
 
-__global__ void k_leaf_flags(const Cells c, int ncells, int32_t* flag) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < ncells) flag[t] = c.left[t] < 0 ? 1 : 0;
+__global__ void k_leaf_flags(const Cells c, const int32_t* __restrict__ counters, int32_t* flag) {
+  const int t_n = counters[C_CELLS];
+  KD_GRID_STRIDE(t, t_n) flag[t] = c.left[t] < 0 ? 1 : 0;
 }
 
 // float32 views of the cells.
-__global__ void k_derive_cells(Cells c, int ncells, float* com_bound) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ncells) return;
+__global__ void k_derive_cells(Cells c, const int32_t* __restrict__ counters, float* com_bound) {
+  const int t_n = counters[C_CELLS];
+  KD_GRID_STRIDE(t, t_n) {
   const double cx = c.cx[t], cy = c.cy[t], cz = c.cz[t];
   c.walk[t] = make_float4((float)cx, (float)cy, (float)cz, (float)c.s[t]);
   c.walk2[t] = make_float2((float)c.hmax[t], __int_as_float(c.skip[t]));
@@ -1134,12 +1170,16 @@ __global__ void k_derive_cells(Cells c, int ncells, float* com_bound) {
   for (int k = 0; k < 6; ++k) s64[4 + k] = c.Q[6 * t + k];
   float b = fmaxf(fabsf((float)cx), fmaxf(fabsf((float)cy), fabsf((float)cz)));
   atomicMax(reinterpret_cast<int*>(com_bound), __float_as_int(b));
+  }
 }
 
-__global__ void k_leaf_list(const Cells c, int ncells, int32_t* leaf_rank, int32_t* leaf_cells,
-                            const int64_t* __restrict__ sys_off, int n_sys, int32_t* leaf_sys) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ncells) return;
+// Leaf ordinal -> cell and system; the leaf count goes to counters[C_LEAVES].
+__global__ void k_leaf_list(const Cells c, int32_t* counters, int32_t* leaf_rank,
+                            int32_t* leaf_cells, const int64_t* __restrict__ sys_off, int n_sys,
+                            int32_t* leaf_sys) {
+  const int t_n = counters[C_CELLS];
+  if (blockIdx.x == 0 && threadIdx.x == 0) counters[C_LEAVES] = leaf_rank[t_n];
+  KD_GRID_STRIDE(t, t_n) {
   if (c.left[t] < 0) {
     const int r = leaf_rank[t];
     leaf_cells[r] = t;
@@ -1147,23 +1187,28 @@ __global__ void k_leaf_list(const Cells c, int ncells, int32_t* leaf_rank, int32
   } else {
     leaf_rank[t] = -1;
   }
+  }
 }
 
 // Per-particle float32 data relative to the centre of mass of its leaf.
-__global__ void k_particles32(const Cells c, const int32_t* __restrict__ leaf_cells, int nleaves,
-                              PCols tp, float4* pf, float4* ph) {
-  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void k_particles32(const Cells c, const int32_t* __restrict__ leaf_cells,
+                              const int32_t* __restrict__ counters, PCols tp, float4* pf,
+                              float4* ph) {
+  const int nleaves = counters[C_LEAVES];
   const int lane = threadIdx.x & 31;
-  if (k >= nleaves) return;
-  const int cell = leaf_cells[k];
-  const int f = c.first[cell], cnt = c.count[cell];
-  if (lane >= cnt) return;
-  const int64_t i = (int64_t)f + lane;
-  pf[i] = make_float4((float)(tp.x[i] - c.cx[cell]), (float)(tp.y[i] - c.cy[cell]),
-                      (float)(tp.z[i] - c.cz[cell]), (float)tp.m[i]);
-  const float h = (float)tp.h[i];
-  const float hi = h > 0.0f ? 1.0f / h : 0.0f;
-  ph[i] = make_float4(hi, hi * hi * hi, h, 0.0f);
+  const int w0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int k = w0; k < nleaves; k += nw) {
+    const int cell = leaf_cells[k];
+    const int f = c.first[cell], cnt = c.count[cell];
+    if (lane >= cnt) continue;
+    const int64_t i = (int64_t)f + lane;
+    pf[i] = make_float4((float)(tp.x[i] - c.cx[cell]), (float)(tp.y[i] - c.cy[cell]),
+                        (float)(tp.z[i] - c.cz[cell]), (float)tp.m[i]);
+    const float h = (float)tp.h[i];
+    const float hi = h > 0.0f ? 1.0f / h : 0.0f;
+    ph[i] = make_float4(hi, hi * hi * hi, h, 0.0f);
+  }
 }
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -1280,12 +1325,42 @@ static int ensure_build_buffers(kdfmm_tree_s* t, int64_t n) {
   return KDFMM_OK;
 }
 
-int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* h, cudaStream_t s) {
+// Launch sizes of the persistent subtree kernel (host calls only; made once
+// per handle and shared-memory size, outside any stream capture).
+static int subtree_setup(kdfmm_tree_s* t, size_t smem) {
+  if (t->subtree_smem == smem) return KDFMM_OK;
+  int rc = check_cuda(cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem),
+                      "subtree smem attribute");
+  if (rc) return rc;
+  int per_sm = 0, sms = 0;
+  rc = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_subtree,
+                                                                 kSubtreeThreads, smem),
+                  "subtree occupancy");
+  if (rc) return rc;
+  rc = check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, t->device), "SMs");
+  if (rc) return rc;
+  t->subtree_grid = std::max(1, per_sm) * std::max(1, sms);
+  t->subtree_smem = smem;
+  return KDFMM_OK;
+}
+
+// Builds the tree (or forest).  fixed_levels <= 0: the host follows the
+// device counters (a synchronisation after the first step, each phase-A
+// level, the subtrees and the numbering) and records the number of phase-A
+// levels in t->levels_used.  fixed_levels > 0: the same launches with no
+// synchronisation -- exactly that many phase-A levels, every launch sized
+// from capacities and reading its count on the device -- so the sequence can
+// be captured in a CUDA graph; a phase A that needed more levels, or any
+// capacity overflow, is left in the status word for the caller to check.
+int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* h, cudaStream_t s,
+               int fixed_levels) {
   const int64_t n = t->n;
+  const bool deferred = fixed_levels > 0;
   int rc = ensure_build_buffers(t, n);
   if (rc) return rc;
   const kdfmm_params& P = t->p;
-  cudaMemsetAsync(t->counters, 0, 16 * sizeof(int32_t), s);
+  cudaMemsetAsync(t->counters, 0, 32 * sizeof(int32_t), s);
   cudaMemsetAsync(t->status, 0, sizeof(int32_t), s);
   cudaMemsetAsync(t->com_bound, 0, sizeof(float), s);
   BuildArgs A{};
@@ -1302,56 +1377,61 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
   t->launches += 2;
 
   int32_t* hc = t->host_counters;
-  rc = check_cuda(cudaMemcpyAsync(hc, t->counters, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
-                  "counters");
-  if (rc) return rc;
-  cudaMemcpyAsync(&t->host_counters[16], t->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-  if ((rc = check_cuda(cudaStreamSynchronize(s), "build init"))) return rc;
-  if (t->host_counters[16] & ST_NONFINITE)
-    return set_error(KDFMM_ERR_NONFINITE, "non-finite position or non-positive mass / h");
-  int nA = hc[1];
+  auto read_back = [&](const char* what) {
+    cudaMemcpyAsync(hc, t->counters, 32 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&hc[32], t->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    return check_cuda(cudaStreamSynchronize(s), what);
+  };
+  if (!deferred) {
+    if ((rc = read_back("build init"))) return rc;
+    if (hc[32] & ST_NONFINITE)
+      return set_error(KDFMM_ERR_NONFINITE, "non-finite position or non-positive mass / h");
+  }
+  // phase A: cells above kSubtreeMax, one level per pass
+  const unsigned maxc = (unsigned)(n / kChunk + t->capA + 1);
+  const unsigned segw = blocks_for(t->capA * 32, 256);
   int cur = 0, level = 0;
-  while (nA > 0) {
+  while (deferred ? level < fixed_levels : hc[C_NEXT_A] > 0) {
     const int src = level & 1, dst = src ^ 1;
     A.src = t->buf[src];
     A.dst = t->buf[dst];
     const Seg* segs = t->segA[cur];
     Seg* next = t->segA[cur ^ 1];
-    cudaMemsetAsync(t->counters + 1, 0, sizeof(int32_t), s);
+    const int32_t* nA = t->counters + C_NA;
+    k_level_begin<<<1, 1, 0, s>>>(t->counters, t->capA, t->status);
     k_chunk_map<<<1, 1024, 0, s>>>(segs, nA, t->seg_chunk_off, t->chunk_seg, t->counters);
-    const unsigned maxc = (unsigned)(n / kChunk + nA + 1);
     k_chunk_reduce<<<maxc, kChunkThreads, 0, s>>>(segs, t->chunk_seg, t->seg_chunk_off, t->counters,
                                                   t->buf[src], t->chunk_sum, t->chunk_key);
-    k_decide<<<blocks_for((int64_t)nA * 32, 256), 256, 0, s>>>(segs, nA, t->seg_chunk_off,
-                                                               t->chunk_sum, t->chunk_key, t->tmp,
-                                                               t->seg_axis, t->seg_cut, t->seg_xb,
-                                                               t->seg_s2);
+    k_decide<<<segw, 256, 0, s>>>(segs, nA, t->seg_chunk_off, t->chunk_sum, t->chunk_key, t->tmp,
+                                  t->seg_axis, t->seg_cut, t->seg_xb, t->seg_s2);
     k_chunk_count<<<maxc, kChunkThreads, 0, s>>>(segs, t->chunk_seg, t->seg_chunk_off, t->counters,
                                                  t->buf[src], t->tmp, t->seg_axis, t->seg_cut,
                                                  t->chunk_left, t->chunk_s2);
-    k_split<<<blocks_for((int64_t)nA * 32, 256), 256, 0, s>>>(
-        segs, nA, t->seg_chunk_off, t->chunk_left, t->chunk_s2, t->chunk_loff, t->seg_nl, t->seg_xb,
-        t->seg_thr2, A, next, t->segB, t->segL, dst);
+    k_split<<<segw, 256, 0, s>>>(segs, nA, t->seg_chunk_off, t->chunk_left, t->chunk_s2,
+                                 t->chunk_loff, t->seg_nl, t->seg_xb, t->seg_thr2, A, next, t->segB,
+                                 t->segL, dst);
     k_chunk_scatter<<<maxc, kChunkThreads, 0, s>>>(segs, t->chunk_seg, t->seg_chunk_off, t->counters,
                                                    t->buf[src], t->buf[dst], t->seg_axis, t->seg_cut,
                                                    t->chunk_loff, t->seg_nl, t->tmp, t->seg_thr2,
                                                    t->seg_s2);
-    k_seg_size<<<blocks_for(nA, 128), 128, 0, s>>>(segs, nA, t->seg_s2, t->tmp);
-    t->launches += 7;
-    rc = check_cuda(cudaMemcpyAsync(hc, t->counters, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
-                    "counters");
-    if (rc) return rc;
-    if ((rc = check_cuda(cudaStreamSynchronize(s), "build level"))) return rc;
-    nA = hc[1];
-    if (nA > t->capA || hc[2] > t->capB || hc[3] > t->capL)
-      return set_error(KDFMM_ERR_CAPACITY, "segment lists overflow");
+    k_seg_size<<<blocks_for(t->capA, 128), 128, 0, s>>>(segs, nA, t->seg_s2, t->tmp);
+    t->launches += 8;
     cur ^= 1;
     ++level;
-    if (level > 200) return set_error(KDFMM_ERR_INTERNAL, "phase A did not terminate");
+    if (!deferred) {
+      if ((rc = read_back("build level"))) return rc;
+      if (hc[32] & ST_CAPACITY) return set_error(KDFMM_ERR_CAPACITY, "segment lists overflow");
+      if (level > 200) return set_error(KDFMM_ERR_INTERNAL, "phase A did not terminate");
+    }
   }
-  const int nB = hc[2], nL = hc[3];
-  if (nB > t->capB || nL > t->capL) return set_error(KDFMM_ERR_CAPACITY, "segment lists overflow");
+  if (deferred) {
+    k_levels_done<<<1, 1, 0, s>>>(t->counters, t->status);
+    t->launches += 1;
+  } else {
+    t->levels_used = level;
+  }
 
+  // phase B: the remaining cells in shared memory, persistent CTAs
   SubArgs S{};
   S.A = A;
   S.buf0 = t->buf[0];
@@ -1359,62 +1439,47 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
   S.out = t->tp;
   S.segB = t->segB;
   S.qcap = kSubtreeMax / (t->min_nleaf + 1) + 2;
-  if (nB > 0) {
-    size_t smem = 4 * kSubtreeMax * sizeof(double) + 3 * kSubtreeMax * sizeof(float) +
-                  2 * kSubtreeMax * sizeof(uint16_t) + 4 * (size_t)S.qcap * sizeof(int4);
-    rc = check_cuda(cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem),
-                    "subtree smem attribute");
-    if (rc) return rc;
-    k_subtree<<<nB, kSubtreeThreads, smem, s>>>(S);
-    t->launches += 1;
+  const size_t smem = 4 * kSubtreeMax * sizeof(double) + 3 * kSubtreeMax * sizeof(float) +
+                      2 * kSubtreeMax * sizeof(uint16_t) + 4 * (size_t)S.qcap * sizeof(int4);
+  if ((rc = subtree_setup(t, smem))) return rc;
+  const int gsub = deferred ? t->subtree_grid : std::max(1, std::min(t->subtree_grid, hc[C_NB]));
+  k_subtree<<<gsub, kSubtreeThreads, smem, s>>>(S);
+  k_leaf_segs<<<kGridBlocks / 4, 128, 0, s>>>(S, t->segL);
+  t->launches += 2;
+  if (!deferred) {
+    if ((rc = read_back("build subtrees"))) return rc;
+    if (hc[32] & ST_NONFINITE)
+      return set_error(KDFMM_ERR_NONFINITE, "non-finite position or non-positive mass / h");
+    if (hc[32] & ST_CAPACITY) return set_error(KDFMM_ERR_CAPACITY, "build capacity exceeded");
+    t->ncells = hc[C_CELLS];
+    t->nfallback = hc[C_FALLBACK];
+    t->depth = hc[C_DEPTH];
   }
-  if (nL > 0) {
-    k_leaf_segs<<<blocks_for((int64_t)nL, 128), 128, 0, s>>>(S, t->segL, nL);
-    t->launches += 1;
-  }
-  rc = check_cuda(cudaMemcpyAsync(hc, t->counters, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
-                  "counters");
-  if (rc) return rc;
-  int32_t status = 0;
-  cudaMemcpyAsync(&t->host_counters[16], t->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-  if ((rc = check_cuda(cudaStreamSynchronize(s), "build subtrees"))) return rc;
-  status = t->host_counters[16];
-  if (status & ST_NONFINITE)
-    return set_error(KDFMM_ERR_NONFINITE, "non-finite position or non-positive mass / h");
-  if (status & ST_CAPACITY) return set_error(KDFMM_ERR_CAPACITY, "build capacity exceeded");
-  const int ncells = hc[0];
-  t->ncells = ncells;
-  t->nfallback = hc[5];
-  t->depth = hc[6];
 
-  // pre-order numbering
+  // pre-order numbering, counts read on the device
   k_fill2<<<blocks_for(n + 1, 256), 256, 0, s>>>(t->cnt_start, 0, t->min_depth, INT_MAX, n + 1);
-  k_count_starts<<<blocks_for(ncells, 256), 256, 0, s>>>(t->tmp, ncells, t->cnt_start, t->min_depth);
+  k_count_starts<<<kGridBlocks, 256, 0, s>>>(t->tmp, t->counters, t->cnt_start, t->min_depth);
   scan_i32(t->cnt_start, t->start_off, n, t->scan_tmp, s);
-  k_remap<<<blocks_for(ncells, 256), 256, 0, s>>>(t->tmp, ncells, t->start_off, t->min_depth, t->c,
-                                                  t->status);
-  k_leaf_flags<<<blocks_for(ncells, 256), 256, 0, s>>>(t->c, ncells, t->c.ready);
-  scan_i32(t->c.ready, t->leaf_rank, ncells, t->scan_tmp, s);
-  cudaMemcpyAsync(&t->host_counters[17], t->leaf_rank + ncells, sizeof(int32_t),
-                  cudaMemcpyDeviceToHost, s);
-  k_leaf_list<<<blocks_for(ncells, 256), 256, 0, s>>>(t->c, ncells, t->leaf_rank, t->leaf_cells,
-                                                      t->sys_off, t->n_sys, t->leaf_sys);
+  k_remap<<<kGridBlocks, 256, 0, s>>>(t->tmp, t->counters, t->start_off, t->min_depth, t->c,
+                                      t->status);
+  k_leaf_flags<<<kGridBlocks, 256, 0, s>>>(t->c, t->counters, t->c.ready);
+  scan_i32_dev(t->c.ready, t->leaf_rank, t->counters + C_CELLS,
+               deferred ? t->cap_cells : (int64_t)t->ncells, t->scan_tmp, s);
+  k_leaf_list<<<kGridBlocks, 256, 0, s>>>(t->c, t->counters, t->leaf_rank, t->leaf_cells,
+                                          t->sys_off, t->n_sys, t->leaf_sys);
   k_sys_roots<<<blocks_for(t->n_sys + 1, 128), 128, 0, s>>>(t->sys_off, t->n_sys, t->start_off,
                                                             t->sys_root);
-  cudaMemcpyAsync(&t->host_counters[16], t->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-  if ((rc = check_cuda(cudaStreamSynchronize(s), "build finalise"))) return rc;
-  t->nleaves = t->host_counters[17];
-  if (t->host_counters[16] & ST_INTERNAL)
-    return set_error(KDFMM_ERR_INTERNAL, "pre-order numbering inconsistent");
-  cudaMemsetAsync(t->c.ready, 0, (size_t)ncells * sizeof(int32_t), s);
-  k_upward<<<blocks_for((int64_t)t->nleaves, 128), 128, 0, s>>>(t->c, t->leaf_cells,
-                                                                     t->nleaves, t->tp);
-  k_derive_cells<<<blocks_for(ncells, 256), 256, 0, s>>>(t->c, ncells, t->com_bound);
-  t->launches += 14;
-  k_particles32<<<blocks_for((int64_t)t->nleaves * 32, 256), 256, 0, s>>>(
-      t->c, t->leaf_cells, t->nleaves, t->tp, t->pf, t->ph);
-  t->launches += 1;
+  if (!deferred) {
+    if ((rc = read_back("build finalise"))) return rc;
+    t->nleaves = hc[C_LEAVES];
+    if (hc[32] & ST_INTERNAL) return set_error(KDFMM_ERR_INTERNAL, "pre-order numbering inconsistent");
+  }
+  cudaMemsetAsync(t->c.ready, 0,
+                  (size_t)(deferred ? t->cap_cells : (int64_t)t->ncells) * sizeof(int32_t), s);
+  k_upward<<<kGridBlocks / 2, 128, 0, s>>>(t->c, t->leaf_cells, t->counters, t->tp);
+  k_derive_cells<<<kGridBlocks, 256, 0, s>>>(t->c, t->counters, t->com_bound);
+  k_particles32<<<kGridBlocks, 256, 0, s>>>(t->c, t->leaf_cells, t->counters, t->tp, t->pf, t->ph);
+  t->launches += 15;
   return check_cuda(cudaGetLastError(), "build launch");
 }
 
@@ -1580,8 +1645,8 @@ int recompute_moments(kdfmm_tree_s* t, const double* x, const double* m, const d
   cudaMemsetAsync(t->c.ready, 0, (size_t)ncells * sizeof(int32_t), s);
   k_upward_frozen<<<blocks_for(nl, 128), 128, 0, s>>>(t->c, t->leaf_cells, nl, Sx, Sy, Sz);
   k_size_frozen<<<blocks_for((int64_t)ncells * 32, 256), 256, 0, s>>>(t->c, ncells, t->tp);
-  k_derive_cells<<<blocks_for(ncells, 256), 256, 0, s>>>(t->c, ncells, t->com_bound);
-  k_particles32<<<blocks_for((int64_t)nl * 32, 256), 256, 0, s>>>(t->c, t->leaf_cells, nl, t->tp,
+  k_derive_cells<<<kGridBlocks, 256, 0, s>>>(t->c, t->counters, t->com_bound);
+  k_particles32<<<kGridBlocks, 256, 0, s>>>(t->c, t->leaf_cells, t->counters, t->tp,
                                                                   t->pf, t->ph);
   t->launches += 6;
   cudaMemcpyAsync(&t->host_counters[16], t->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);

@@ -24,7 +24,31 @@ enum : int {
   ST_CAPACITY = 2,
   ST_INTERNAL = 4,
   ST_TIMEOUT = 8,
+  ST_UNFINISHED = 16,   // phase A still held segments after its fixed number of levels
+  ST_LISTS = 32,        // the leaves or an interaction list outgrew a fixed capacity
 };
+
+// Slots of the handle's device counter block (32 int32).  Kernels read the
+// sizes they work on from here, so a launch needs no host-side count.
+enum : int {
+  C_CELLS = 0,      // cells allocated
+  C_NEXT_A = 1,     // segments pushed for the next phase-A level
+  C_NB = 2,         // phase-B segments
+  C_NL = 3,         // leaf segments finished by phase A
+  C_CHUNKS = 4,     // chunks of the current phase-A level
+  C_FALLBACK = 5,   // degenerate cuts
+  C_DEPTH = 6,      // deepest level
+  C_MAXFAR = 8,     // longest far list of the last walk
+  C_MAXNEAR = 9,    // longest near list of the last walk
+  C_NA = 10,        // segments of the current phase-A level
+  C_LEAVES = 11,    // leaves
+  C_WORK = 12,      // dynamic work counter of the persistent subtree kernel
+};
+
+// Grid of the grid-stride (persistent) kernels: blocks per SM x SMs of a GB300.
+constexpr int kGridBlocks = 152 * 8;
+#define KD_GRID_STRIDE(i, n)                                                             \
+  for (int i = (int)(blockIdx.x * blockDim.x + threadIdx.x); i < (n); i += (int)(gridDim.x * blockDim.x))
 
 // A contiguous run of tree positions that belongs to one cell during the build.
 struct Seg {
@@ -79,6 +103,10 @@ struct kdfmm_tree_s {
   int device = 0;
   int64_t n = 0, cap_n = 0;
   int32_t ncells = 0, nleaves = 0, depth = 0, nfallback = 0;
+  int32_t grid_leaves = 0;         // leaves the launches of an evaluation are sized for
+  int32_t levels_used = 0;         // phase-A levels of the last host-followed build
+  int32_t subtree_grid = 0;        // persistent grid of the subtree kernel
+  size_t subtree_smem = 0;
   int64_t cap_cells = 0;
   kdfmm_params p{};
   bool built = false, evaluated = false, lists_frozen = false;
@@ -139,6 +167,28 @@ struct kdfmm_tree_s {
   int64_t* host_stats = nullptr;   // pinned host mirror
   int32_t* host_counters = nullptr;
   int64_t launches = 0;            // kernels launched by this handle
+
+  // captured evaluation (kdfmm_fmm_accel_batched): valid for the arguments
+  // and buffers it was captured with
+  struct GraphKey {
+    const void *x, *m, *h;
+    void *a, *phi;
+    int64_t n, cap_n, cap_far, cap_near, far_cap, near_cap;
+    int32_t n_sys, cap_sys, min_nleaf, soft_kind, precision;
+    double r_kern;
+    bool operator==(const GraphKey& o) const {
+      return x == o.x && m == o.m && h == o.h && a == o.a && phi == o.phi && n == o.n &&
+             cap_n == o.cap_n && cap_far == o.cap_far && cap_near == o.cap_near &&
+             far_cap == o.far_cap && near_cap == o.near_cap && n_sys == o.n_sys &&
+             cap_sys == o.cap_sys && min_nleaf == o.min_nleaf && soft_kind == o.soft_kind &&
+             precision == o.precision && r_kern == o.r_kern;
+    }
+  };
+  GraphKey graph_key{};
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  int32_t graph_levels = 0, graph_leaves = 0;
+  int64_t graph_launches = 0;      // kernels in the captured graph
   bool timing = false;
   cudaEvent_t ev[2 * KDFMM_NPHASES]{};
   bool ev_used[KDFMM_NPHASES]{};
@@ -325,10 +375,14 @@ __device__ __forceinline__ int system_of(const int64_t* __restrict__ off, int n_
 // Host-side launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
 int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* h,
-               cudaStream_t s);
+               cudaStream_t s, int fixed_levels);
 int recompute_moments(kdfmm_tree_s* t, const double* x, const double* m, const double* h,
                       cudaStream_t s);
 int run_walk(kdfmm_tree_s* t, cudaStream_t s);
+// walk into the current slot capacities without synchronising or allocating
+// (ensure_slots first; overflow is flagged in the status word)
+int ensure_slots(kdfmm_tree_s* t, int slot_leaves);
+int walk_fixed(kdfmm_tree_s* t, int slot_leaves, cudaStream_t s);
 int run_m2l(kdfmm_tree_s* t, cudaStream_t s);
 int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s);
 int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, cudaStream_t s);
@@ -336,6 +390,9 @@ int momentum(const double* m, const double* v, int64_t n, double* out, double* s
              cudaStream_t s);
 // exclusive scan of n int32 (out may alias in); returns the total in *total_dev
 void scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, cudaStream_t s);
+// the same with the count read from device memory (*n_dev <= cap)
+void scan_i32_dev(const int32_t* in, int32_t* out, const int32_t* n_dev, int64_t cap, int32_t* tmp,
+                  cudaStream_t s);
 void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s);
 int64_t scan_tmp_elems(int64_t n);
 

@@ -20,6 +20,9 @@
 // works in float32 with the centre-of-mass difference formed from
 // (high, low) float pairs and compensated sums for C0 and C1; FP64 mode works
 // in float64 throughout.
+#include <algorithm>
+#include <climits>
+
 #include "kdfmm_internal.cuh"
 
 namespace kdfmm {
@@ -98,7 +101,9 @@ __device__ __forceinline__ void m2l_coeffs(T Rx, T Ry, T Rz, T M, const T Q[6], 
 
 struct M2LArgs {
   const int32_t* leaf_cells;
-  int nleaves;
+  const int32_t* counters;   // counters[C_LEAVES]: leaves
+  int64_t cap_far;           // entries a list may hold (slot size, or no limit)
+  int max_leaves;            // leaves the lists were made for
   const int32_t* far_cnt;
   const int32_t* far_idx;
   const int64_t* far_off;
@@ -109,9 +114,10 @@ struct M2LArgs {
 };
 
 __global__ void __launch_bounds__(256) k_m2l_mixed(M2LArgs A) {
-  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (k >= A.nleaves) return;
+  const int nleaves = min(A.counters[C_LEAVES], A.max_leaves);
+  for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < nleaves;
+       k += (int)((gridDim.x * blockDim.x) >> 5)) {
   const int a = A.leaf_cells[k];
   const float4 ah = A.src32[4 * a], al = A.src32[4 * a + 1];
   float acc[20], lo[4];
@@ -119,7 +125,7 @@ __global__ void __launch_bounds__(256) k_m2l_mixed(M2LArgs A) {
   for (int j = 0; j < 20; ++j) acc[j] = 0.0f;
 #pragma unroll
   for (int j = 0; j < 4; ++j) lo[j] = 0.0f;
-  const int64_t off = A.far_off[k], nf = A.far_cnt[k];
+  const int64_t off = A.far_off[k], nf = min((int64_t)A.far_cnt[k], A.cap_far);
   for (int64_t e = lane; e < nf; e += 32) {
     const int b = A.far_idx[off + e];
     const float4 b0 = A.src32[4 * b], b1 = A.src32[4 * b + 1], b2 = A.src32[4 * b + 2],
@@ -158,19 +164,21 @@ __global__ void __launch_bounds__(256) k_m2l_mixed(M2LArgs A) {
     for (int j = 1; j < 4; ++j) v = lane - 20 == j ? lo[j] : v;
     out[lane] = v;
   }
+  }
 }
 
 __global__ void __launch_bounds__(256) k_m2l_fp64(M2LArgs A) {
-  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (k >= A.nleaves) return;
+  const int nleaves = min(A.counters[C_LEAVES], A.max_leaves);
+  for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < nleaves;
+       k += (int)((gridDim.x * blockDim.x) >> 5)) {
   const int a = A.leaf_cells[k];
   const double* sa = A.src64 + 10 * (int64_t)a;
   const double ax = sa[0], ay = sa[1], az = sa[2];
   double acc[20];
 #pragma unroll
   for (int j = 0; j < 20; ++j) acc[j] = 0.0;
-  const int64_t off = A.far_off[k], nf = A.far_cnt[k];
+  const int64_t off = A.far_off[k], nf = min((int64_t)A.far_cnt[k], A.cap_far);
   for (int64_t e = lane; e < nf; e += 32) {
     const int b = A.far_idx[off + e];
     const double* sb = A.src64 + 10 * (int64_t)b;
@@ -191,6 +199,7 @@ __global__ void __launch_bounds__(256) k_m2l_fp64(M2LArgs A) {
     for (int j = 1; j < 20; ++j) v = lane == j ? acc[j] : v;
     out[lane] = v;
   }
+  }
 }
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -200,7 +209,9 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 int run_m2l(kdfmm_tree_s* t, cudaStream_t s) {
   M2LArgs A{};
   A.leaf_cells = t->leaf_cells;
-  A.nleaves = t->nleaves;
+  A.counters = t->counters;
+  A.cap_far = t->L.exact ? INT64_MAX : t->L.cap_far;
+  A.max_leaves = std::max(t->grid_leaves, 1);
   A.far_cnt = t->L.far_cnt;
   A.far_off = t->L.far_off;
   A.far_idx = t->L.far_idx;
@@ -208,7 +219,7 @@ int run_m2l(kdfmm_tree_s* t, cudaStream_t s) {
   A.src64 = t->c.src64;
   A.lexp32 = t->lexp32;
   A.lexp64 = t->lexp64;
-  const unsigned g = blocks_for((int64_t)t->nleaves * 32, 256);
+  const unsigned g = blocks_for((int64_t)std::max(t->grid_leaves, 1) * 32, 256);
   if (t->p.precision == KDFMM_MIXED) k_m2l_mixed<<<g, 256, 0, s>>>(A);
   else k_m2l_fp64<<<g, 256, 0, s>>>(A);
   t->launches += 1;

@@ -20,6 +20,9 @@
 // float32 arithmetic.  Each near leaf's contribution is summed in float32 and
 // folded into a (high, low) accumulator with two-sum; the long-range part is
 // added in float64 at the end.  FP64 mode uses float64 absolute positions.
+#include <algorithm>
+#include <climits>
+
 #include "kdfmm_internal.cuh"
 
 namespace kdfmm {
@@ -28,7 +31,9 @@ namespace {
 
 struct P2PArgs {
   const int32_t* leaf_cells;
-  int nleaves;
+  const int32_t* counters;   // counters[C_LEAVES]: leaves
+  int64_t cap_near;          // entries a list may hold (slot size, or no limit)
+  int max_leaves;            // leaves the lists were made for
   const int32_t *cfirst, *ccount;
   const int32_t* near_cnt;
   const int32_t* near_idx;
@@ -263,8 +268,8 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
   __shared__ int s_tbeg[kP2PWarps][32], s_tfirst[kP2PWarps][32];   // chunk's leaves: staged start, first
   __shared__ float4 s_toff[kP2PWarps][32];                          // and offset to the target com
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k = blockIdx.x * kP2PWarps + warp;
-  if (k >= A.nleaves) return;
+  const int nleaves = min(A.counters[C_LEAVES], A.max_leaves);
+  for (int k = blockIdx.x * kP2PWarps + warp; k < nleaves; k += gridDim.x * kP2PWarps) {
   float4* sp = s_pos[warp];
   float4* sk = s_ker[M4 ? warp : 0];
   int* tb = s_tbeg[warp];
@@ -290,7 +295,7 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
     df_add(axh, axl, fx); df_add(ayh, ayl, fy); df_add(azh, azl, fz); df_add(ph_, pl, fp);
   }
   const unsigned full = 0xffffffffu, lt = (1u << lane) - 1u;
-  const int64_t e1 = A.near_off[k] + A.near_cnt[k];
+  const int64_t e1 = A.near_off[k] + min((int64_t)A.near_cnt[k], A.cap_near);
   for (int64_t e = A.near_off[k]; e < e1;) {
     // up to 32 candidate leaves, one per lane
     const int64_t my = e + lane;
@@ -439,7 +444,7 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
       df_add2(ph_, pl, bph, bpl);
     }
   }
-  if (sl != 0 || !act) return;
+  if (sl != 0 || !act) continue;
   const float* C = A.lexp32 + 24 * (int64_t)k;
   float tx, ty, tz, tp_;
   l2p_tail<float>(C, xa.x, xa.y, xa.z, tx, ty, tz, tp_);
@@ -451,13 +456,15 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
   A.a[3 * ci + 1] = ay;
   A.a[3 * ci + 2] = az;
   if (A.phi) A.phi[ci] = (double)ph_ + (double)pl + ((double)C[0] + (double)C[20]) + (double)tp_;
+  }
 }
 
 template <int SOFT>
 __global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
-  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (k >= A.nleaves) return;
+  const int nleaves = min(A.counters[C_LEAVES], A.max_leaves);
+  for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < nleaves;
+       k += (int)((gridDim.x * blockDim.x) >> 5)) {
   const int a = A.leaf_cells[k];
   const int fa = A.cfirst[a], nt = A.ccount[a];
   const int K = 32 / nt;
@@ -468,7 +475,7 @@ __global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
   const double eps = A.sys_eps[A.leaf_sys[k]];
   const double eps2 = eps * eps;
   double fx = 0.0, fy = 0.0, fz = 0.0, fp = 0.0;
-  const int64_t e0 = A.near_off[k], e1 = e0 + A.near_cnt[k];
+  const int64_t e0 = A.near_off[k], e1 = e0 + min((int64_t)A.near_cnt[k], A.cap_near);
   if (act) {
     for (int64_t e = e0; e < e1; ++e) {
       const int b = A.near_idx[e];
@@ -487,7 +494,7 @@ __global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
     const double bz = __shfl_sync(0xffffffffu, fz, src), bp = __shfl_sync(0xffffffffu, fp, src);
     if (sl == 0) { fx += bx; fy += by; fz += bz; fp += bp; }
   }
-  if (sl != 0 || !act) return;
+  if (sl != 0 || !act) continue;
   const double* C = A.lexp64 + 20 * (int64_t)k;
   const double x = xi - A.cx[a], y = yi - A.cy[a], z = zi - A.cz[a];
   double tx, ty, tz, tp_;
@@ -497,6 +504,7 @@ __global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
   A.a[3 * ci + 1] = fy + (ty - C[2]);
   A.a[3 * ci + 2] = fz + (tz - C[3]);
   if (A.phi) A.phi[ci] = fp + (C[0] + tp_);
+  }
 }
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -506,7 +514,9 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s) {
   P2PArgs A{};
   A.leaf_cells = t->leaf_cells;
-  A.nleaves = t->nleaves;
+  A.counters = t->counters;
+  A.cap_near = t->L.exact ? INT64_MAX : t->L.cap_near;
+  A.max_leaves = std::max(t->grid_leaves, 1);
   A.cfirst = t->c.first;
   A.ccount = t->c.count;
   A.near_cnt = t->L.near_cnt;
@@ -525,10 +535,11 @@ int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s) {
   A.sys_eps = t->sys_eps;
   A.a = a;
   A.phi = phi;
-  const unsigned g = blocks_for((int64_t)t->nleaves * 32, 256);
+  const int gl = std::max(t->grid_leaves, 1);
+  const unsigned g = blocks_for((int64_t)gl * 32, 256);
   const bool m4 = t->p.soft_kind == KDFMM_SOFT_M4;
   if (t->p.precision == KDFMM_MIXED) {
-    const unsigned gm = blocks_for(t->nleaves, kP2PWarps);
+    const unsigned gm = blocks_for(gl, kP2PWarps);
     if (m4) k_p2p_mixed<KDFMM_SOFT_M4><<<gm, kP2PWarps * 32, 0, s>>>(A);
     else k_p2p_mixed<KDFMM_SOFT_PLUMMER><<<gm, kP2PWarps * 32, 0, s>>>(A);
   } else {

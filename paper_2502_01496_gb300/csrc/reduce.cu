@@ -23,10 +23,13 @@ __device__ __forceinline__ T warp_incl_scan(T v) {
 }
 
 // Exclusive scan of one tile per block; the block total goes to tot[block].
+// n_dev, when given, holds the element count (at most n); the launch is sized
+// for n.
 template <class TO>
 __global__ void k_scan_tile(const int32_t* __restrict__ in, TO* __restrict__ out, int64_t n,
-                            TO* __restrict__ tot) {
+                            const int32_t* __restrict__ n_dev, TO* __restrict__ tot) {
   __shared__ TO warp_tot[kScanThreads / 32];
+  if (n_dev) n = *n_dev;
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
   TO v[kScanPer];
   TO run = 0;
@@ -86,8 +89,9 @@ __global__ void k_scan_top(TO* tot, int64_t nb) {
 }
 
 template <class TO>
-__global__ void k_scan_add(TO* __restrict__ out, int64_t n, const TO* __restrict__ tot,
-                           int64_t nb) {
+__global__ void k_scan_add(TO* __restrict__ out, int64_t n, const int32_t* __restrict__ n_dev,
+                           const TO* __restrict__ tot, int64_t nb) {
+  if (n_dev) n = *n_dev;
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   const TO off = tot[blockIdx.x];
   for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
@@ -98,15 +102,16 @@ __global__ void k_scan_add(TO* __restrict__ out, int64_t n, const TO* __restrict
 }
 
 template <class TO>
-void scan_impl(const int32_t* in, TO* out, int64_t n, TO* tmp, cudaStream_t s) {
+void scan_impl(const int32_t* in, TO* out, int64_t n, const int32_t* n_dev, TO* tmp,
+               cudaStream_t s) {
   int64_t nb = (n + kScanTile - 1) / kScanTile;
   if (nb == 0) {
     cudaMemsetAsync(out, 0, sizeof(TO), s);
     return;
   }
-  k_scan_tile<TO><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, tmp);
+  k_scan_tile<TO><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, n_dev, tmp);
   k_scan_top<TO><<<1, 1024, 0, s>>>(tmp, nb);
-  k_scan_add<TO><<<(unsigned)nb, kScanThreads, 0, s>>>(out, n, tmp, nb);
+  k_scan_add<TO><<<(unsigned)nb, kScanThreads, 0, s>>>(out, n, n_dev, tmp, nb);
 }
 
 // ---------------------------------------------------------------------------
@@ -185,11 +190,16 @@ __global__ void k_momentum_final(const double* __restrict__ part, int nb, double
 int64_t scan_tmp_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 2; }
 
 void scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, cudaStream_t s) {
-  scan_impl<int32_t>(in, out, n, tmp, s);
+  scan_impl<int32_t>(in, out, n, nullptr, tmp, s);
+}
+
+void scan_i32_dev(const int32_t* in, int32_t* out, const int32_t* n_dev, int64_t cap, int32_t* tmp,
+                  cudaStream_t s) {
+  scan_impl<int32_t>(in, out, cap, n_dev, tmp, s);
 }
 
 void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s) {
-  scan_impl<int64_t>(in, out, n, tmp, s);
+  scan_impl<int64_t>(in, out, n, nullptr, tmp, s);
 }
 
 int64_t momentum_blocks(int64_t n) {

@@ -15,6 +15,7 @@
 // cotangents (M_bar, com_bar, Q_bar) give m_bar_i and x_bar_i as a quadratic
 // polynomial in x_i, summed over the leaf's chain of ancestors.
 #include <algorithm>
+#include <climits>
 
 #include "kdfmm_internal.cuh"
 
@@ -154,6 +155,7 @@ struct VjpArgs {
   const double* lexp64;
   const int32_t *far_cnt, *far_idx, *near_cnt, *near_idx;
   const int64_t *far_off, *near_off;
+  int64_t cap_far, cap_near;            // entries a list may hold
   double* ab;                           // cotangent in tree order (N x 3)
   double* xbar;                         // tree order (N x 3)
   double* mbar;                         // tree order (N)
@@ -255,7 +257,7 @@ __global__ void k_vjp_m2l(VjpArgs V) {
   const double ax = V.c.cx[a], ay = V.c.cy[a], az = V.c.cz[a];
   double rx = 0.0, ry = 0.0, rz = 0.0;
   const int64_t off = V.far_off[k];
-  const int nf = V.far_cnt[k];
+  const int nf = (int)min((int64_t)V.far_cnt[k], V.cap_far);
   const double zq[6] = {0, 0, 0, 0, 0, 0};
   for (int e = lane; e < nf; e += 32) {
     const int b = V.far_idx[off + e];
@@ -362,7 +364,7 @@ __global__ void k_vjp_p2p(VjpArgs V) {
   const double eps = V.sys_eps[V.leaf_sys[k]], eps2 = eps * eps;
   double gx = 0.0, gy = 0.0, gz = 0.0;
   const int64_t e0 = V.near_off[k];
-  const int nn = V.near_cnt[k];
+  const int nn = (int)min((int64_t)V.near_cnt[k], V.cap_near);
   for (int e = 0; e < nn; ++e) {
     const int bc = V.near_idx[e0 + e];
     const int fb = V.c.first[bc], nb = V.c.count[bc];
@@ -495,6 +497,8 @@ int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, 
   V.far_cnt = t->L.far_cnt; V.far_idx = t->L.far_idx;
   V.near_cnt = t->L.near_cnt; V.near_idx = t->L.near_idx;
   V.far_off = t->L.far_off; V.near_off = t->L.near_off;
+  V.cap_far = t->L.exact ? INT64_MAX : t->L.cap_far;
+  V.cap_near = t->L.exact ? INT64_MAX : t->L.cap_near;
   double* dp = reinterpret_cast<double*>(buf);
   V.ab = dp; dp += 3 * n;
   V.xbar = dp; dp += 3 * n;

@@ -32,7 +32,9 @@ struct WalkArgs {
   const double *cx, *cy, *cz, *s, *hmax;
   const int32_t* count;
   const int32_t* leaf_cells;
-  int nleaves, ncells;
+  const int32_t* counters;         // counters[C_LEAVES]: leaves to walk
+  int slot_leaves;                 // slot mode: leaves the slots were allocated for
+  int32_t* status;
   const float* com_bound;
   const int32_t* leaf_sys;         // system of each leaf
   const int32_t* sys_root;         // first cell of each system (+ end)
@@ -81,8 +83,14 @@ __device__ __forceinline__ int open_filter(float4 a, float ha, float4 b, float h
 // then grows the slots and walks again, or switches to exact mode).  Exact
 // mode: the counts of a previous pass, scanned, give each leaf's start.
 __global__ void __launch_bounds__(128) k_walk(WalkArgs W) {
+  // the grid covers slot_leaves leaves; more leaves than slots is flagged and
+  // the evaluation is redone by the host
+  const int nleaves = W.counters[C_LEAVES];
+  if (!W.exact && nleaves > W.slot_leaves && blockIdx.x == 0 && threadIdx.x == 0)
+    atomicOr(W.status, ST_LISTS);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= W.nleaves) return;
+  if (k >= nleaves || (!W.exact && k >= W.slot_leaves)) return;
+  {
   const int a = W.leaf_cells[k];
   const float4 wa = W.walk[a];
   const float ha = W.walk2[a].x;
@@ -142,19 +150,31 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs W) {
   atomicAdd(&W.stats[2], (unsigned long long)nf);
   atomicAdd(&W.stats[3], (unsigned long long)nn);
   if (nex) atomicAdd(&W.stats[1], (unsigned long long)nex);
+  }
 }
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
 
-static int ensure_idx(int32_t** idx, int64_t* have, int64_t need, const char* what) {
+// Grows a list buffer to `need` entries; with `keep` the entries already
+// there are copied over (the slot layout does not depend on the size).
+static int ensure_idx(int32_t** idx, int64_t* have, int64_t need, const char* what,
+                      bool keep = false) {
   if (*have >= need) return KDFMM_OK;
-  cudaFree(*idx);
-  *idx = nullptr;
-  *have = 0;
-  if (cudaMalloc(idx, (size_t)std::max<int64_t>(need, 1) * sizeof(int32_t)) != cudaSuccess)
+  int32_t* fresh = nullptr;
+  if (cudaMalloc(&fresh, (size_t)std::max<int64_t>(need, 1) * sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
     return set_error(KDFMM_ERR_OOM, "%s (%lld entries)", what, (long long)need);
+  }
+  if (keep && *idx != nullptr && *have > 0 &&
+      cudaMemcpy(fresh, *idx, (size_t)*have * sizeof(int32_t), cudaMemcpyDeviceToDevice) !=
+          cudaSuccess) {
+    cudaFree(fresh);
+    return check_cuda(cudaGetLastError(), "list copy");
+  }
+  cudaFree(*idx);
+  *idx = fresh;
   *have = need;
   return KDFMM_OK;
 }
@@ -171,18 +191,16 @@ static bool force_exact_lists() {
   return v != nullptr && strcmp(v, "exact") == 0;
 }
 
-int run_walk(kdfmm_tree_s* t, cudaStream_t s) {
-  const int nl = t->nleaves;
+static WalkArgs walk_args(kdfmm_tree_s* t) {
   Lists& L = t->L;
-  int64_t cf = L.cap_far > 0 ? L.cap_far : 512, cn = L.cap_near > 0 ? L.cap_near : 128;
   WalkArgs W{};
   W.walk = t->c.walk;
   W.walk2 = t->c.walk2;
   W.cx = t->c.cx; W.cy = t->c.cy; W.cz = t->c.cz; W.s = t->c.s; W.hmax = t->c.hmax;
   W.count = t->c.count;
   W.leaf_cells = t->leaf_cells;
-  W.nleaves = nl;
-  W.ncells = t->ncells;
+  W.counters = t->counters;
+  W.status = t->status;
   W.com_bound = t->com_bound;
   W.leaf_sys = t->leaf_sys;
   W.sys_root = t->sys_root;
@@ -192,21 +210,57 @@ int run_walk(kdfmm_tree_s* t, cudaStream_t s) {
   W.near_cnt = L.near_cnt;
   W.far_off = L.far_off;
   W.near_off = L.near_off;
-  W.maxc = t->counters + 8;
+  W.maxc = t->counters + C_MAXFAR;
   W.stats = reinterpret_cast<unsigned long long*>(L.near_np);
+  return W;
+}
+
+// One walk into the current slots (or exact lists), no synchronisation.
+static void walk_launch(kdfmm_tree_s* t, WalkArgs W, bool exact, int64_t cf, int64_t cn,
+                        int slot_leaves, cudaStream_t s) {
+  Lists& L = t->L;
+  W.exact = exact;
+  W.far_idx = L.far_idx;
+  W.near_idx = L.near_idx;
+  W.cap_far = cf;
+  W.cap_near = cn;
+  W.slot_leaves = slot_leaves;
+  cudaMemsetAsync(L.near_np, 0, 4 * sizeof(int64_t), s);
+  cudaMemsetAsync(t->counters + C_MAXFAR, 0, 2 * sizeof(int32_t), s);
+  k_walk<<<blocks_for(std::max(slot_leaves, 1), 128), 128, 0, s>>>(W);
+  t->launches += 1;
+}
+
+int ensure_slots(kdfmm_tree_s* t, int slot_leaves) {
+  Lists& L = t->L;
+  int rc;
+  if ((rc = ensure_idx(&L.far_idx, &L.far_cap, (int64_t)slot_leaves * L.cap_far, "far list slots",
+                       true)))
+    return rc;
+  return ensure_idx(&L.near_idx, &L.near_cap, (int64_t)slot_leaves * L.cap_near,
+                    "near list slots", true);
+}
+
+int walk_fixed(kdfmm_tree_s* t, int slot_leaves, cudaStream_t s) {
+  Lists& L = t->L;
+  if (L.far_cap < (int64_t)slot_leaves * L.cap_far || L.near_cap < (int64_t)slot_leaves * L.cap_near)
+    return set_error(KDFMM_ERR_INTERNAL, "list slots not allocated for %d leaves", slot_leaves);
+  L.exact = false;
+  walk_launch(t, walk_args(t), false, L.cap_far, L.cap_near, slot_leaves, s);
+  return check_cuda(cudaGetLastError(), "walk launch");
+}
+
+int run_walk(kdfmm_tree_s* t, cudaStream_t s) {
+  const int nl = t->nleaves;
+  Lists& L = t->L;
+  int64_t cf = L.cap_far > 0 ? L.cap_far : 512, cn = L.cap_near > 0 ? L.cap_near : 128;
+  WalkArgs W = walk_args(t);
   int32_t* hc = t->host_counters;
   int rc;
   auto launch = [&](bool exact) {
-    W.exact = exact;
-    W.far_idx = L.far_idx;
-    W.near_idx = L.near_idx;
-    W.cap_far = cf;
-    W.cap_near = cn;
-    cudaMemsetAsync(L.near_np, 0, 4 * sizeof(int64_t), s);
-    cudaMemsetAsync(t->counters + 8, 0, 2 * sizeof(int32_t), s);
-    k_walk<<<blocks_for(nl, 128), 128, 0, s>>>(W);
-    t->launches += 1;
-    cudaMemcpyAsync(hc + 8, t->counters + 8, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    walk_launch(t, W, exact, cf, cn, nl, s);
+    cudaMemcpyAsync(hc + C_MAXFAR, t->counters + C_MAXFAR, 2 * sizeof(int32_t),
+                    cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(t->host_stats + 16, L.near_np, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     return check_cuda(cudaStreamSynchronize(s), "walk");
   };
@@ -215,7 +269,7 @@ int run_walk(kdfmm_tree_s* t, cudaStream_t s) {
     if ((rc = ensure_idx(&L.far_idx, &L.far_cap, (int64_t)nl * cf, "far list slots"))) return rc;
     if ((rc = ensure_idx(&L.near_idx, &L.near_cap, (int64_t)nl * cn, "near list slots"))) return rc;
     if ((rc = launch(false))) return rc;
-    const int64_t mf = hc[8], mn = hc[9];
+    const int64_t mf = hc[C_MAXFAR], mn = hc[C_MAXNEAR];
     const int64_t tot_far = t->host_stats[16 + 2], tot_near = t->host_stats[16 + 3];
     if (mf <= cf && mn <= cn && !force_exact) {
       L.cap_far = cf;

@@ -177,3 +177,52 @@ def test_exact_lists_match_slots(oracle, monkeypatch, prec):
     for k, ps in enumerate(systems):
         T = oracle.Tree(ps.x, ps.m, None, theta=theta[k], n_leaf=n_leaf[k], soft_kind=0, eps=eps[k])
         assert_lists_bit_exact({"ex": parts[k]}, {"lists": T.walk()})
+
+
+def _batched(f, x, m, off, theta, n_leaf, a, phi):
+    from paper_2502_01496_gb300 import native
+    native.fmm_accel_batched(f.handle, x, m, None, off, f.params, a, phi, theta=theta,
+                             eps=np.full(len(off) - 1, 0.01), n_leaf=n_leaf)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_captured_graph_replays_the_eager_evaluation(monkeypatch, prec):
+    """Repeated batched calls on the same buffers: the first runs eagerly and
+    captures a graph, later ones replay it.  Replays give the eager bits, and
+    a replay whose trees outgrow the graph (longer lists after theta drops,
+    other system sizes) falls back to the eager path with the same results as
+    a handle that never used a graph."""
+    import torch
+    from paper_2502_01496_gb300 import native
+    systems = [W.plummer(n, W.seed_for(3, 990 + k)) for k, n in enumerate([5000, 3000, 1200, 6000])]
+    x0, m0, _, off = _concat(systems)
+    n = x0.shape[0]
+    x, m = _cuda(x0), _cuda(m0)
+    a = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    phi = torch.empty(n, dtype=torch.float64, device="cuda")
+    n_leaf = np.array([16, 12, 8, 16], dtype=np.int32)
+
+    def reference(theta, offs):
+        monkeypatch.setenv("KDFMM_GRAPH", "0")
+        g = native.KdFmm(theta=0.5, eps=0.01, n_leaf=16, soft_kind=0, precision=prec)
+        ar = torch.empty_like(a)
+        pr = torch.empty_like(phi)
+        _batched(g, x, m, offs, theta, n_leaf, ar, pr)
+        torch.cuda.synchronize()
+        monkeypatch.delenv("KDFMM_GRAPH")
+        return ar.cpu().numpy(), pr.cpu().numpy(), g.stats()
+
+    f = native.KdFmm(theta=0.5, eps=0.01, n_leaf=16, soft_kind=0, precision=prec)
+    cases = [(np.full(4, 1.0), off), (np.full(4, 1.0), off), (np.full(4, 1.0), off),
+             (np.array([0.3, 0.4, 0.35, 0.3]), off),                       # longer lists
+             (np.array([0.3, 0.4, 0.35, 0.3]), off),
+             (np.full(4, 0.6), np.array([0, 200, 9000, 9100, n], dtype=np.int64))]   # other sizes
+    for theta, offs in cases:
+        _batched(f, x, m, offs, theta, n_leaf, a, phi)
+        torch.cuda.synchronize()
+        ra, rp, rst = reference(theta, offs)
+        assert np.array_equal(a.cpu().numpy(), ra)
+        assert np.array_equal(phi.cpu().numpy(), rp)
+        st = f.stats()
+        for key in ("ncells", "nleaves", "depth", "nfar", "nnear", "np2p"):
+            assert st[key] == rst[key], (key, st[key], rst[key])
