@@ -187,7 +187,30 @@ static int build_common(kdfmm_tree_s* t, const double* x, const double* m, const
   const int64_t old_cap = t->cap_n;
   int rc;
   phase_begin(t, KDFMM_PHASE_BUILD, s);
-  if ((rc = build_tree(t, x, m, h, s, 0))) return rc;
+  // After a first build the handle knows how many phase-A levels a tree of
+  // this kind needs: build without synchronising (one more level as margin)
+  // and read the counters once; a tree that needed more levels is rebuilt
+  // with the host following the counters.
+  bool done = false;
+  if (t->levels_used > 0 && t->cap_n >= n) {
+    if ((rc = build_tree(t, x, m, h, s, t->levels_used + 1))) return rc;
+    int32_t* hc = t->host_counters;
+    cudaMemcpyAsync(hc, t->counters, 32 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&hc[32], t->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if ((rc = check_cuda(cudaStreamSynchronize(s), "build"))) return rc;
+    const int32_t st = hc[32];
+    if (st & ST_NONFINITE)
+      return set_error(KDFMM_ERR_NONFINITE, "non-finite position or non-positive mass / h");
+    if (st & ST_INTERNAL) return set_error(KDFMM_ERR_INTERNAL, "pre-order numbering inconsistent");
+    if (!(st & (ST_UNFINISHED | ST_CAPACITY))) {
+      t->ncells = hc[C_CELLS];
+      t->nleaves = hc[C_LEAVES];
+      t->depth = hc[C_DEPTH];
+      t->nfallback = hc[C_FALLBACK];
+      done = true;
+    }
+  }
+  if (!done && (rc = build_tree(t, x, m, h, s, 0))) return rc;
   phase_end(t, KDFMM_PHASE_BUILD, s);
   t->grid_leaves = t->nleaves;
   if (t->cap_n != old_cap || t->L.far_cnt == nullptr)

@@ -165,3 +165,35 @@ def test_invalid_arguments_return_status_codes():
     a, _ = f.accel()
     torch.cuda.synchronize()
     assert torch.isfinite(a).all()
+
+
+def test_rebuilds_match_fresh_handles(oracle):
+    """A handle's second and later builds run without host synchronisation
+    (as many phase-A levels as the last host-followed build, plus one); a tree
+    that needs more levels is rebuilt with the host following the counters.
+    Either way the tree, lists and forces equal those of a fresh handle."""
+    import torch
+    from paper_2502_01496_gb300 import native
+    from paper_2502_01496_gb300 import workloads as W
+    sets = [W.plummer(20000, W.seed_for(0, 70)),           # few levels
+            W.plummer(20000, W.seed_for(0, 71)),           # same shape: deferred build
+            W.uniform_clumps(300000, W.seed_for(0, 72)),   # more levels: falls back
+            W.uniform_clumps(300000, W.seed_for(0, 73))]
+    f = native.KdFmm(theta=0.5, eps=0.01, n_leaf=16, soft_kind=0, precision=1)
+    for ps in sets:
+        x = torch.tensor(ps.x, device="cuda")
+        m = torch.tensor(ps.m, device="cuda")
+        f.params = native.make_params(theta=0.5, eps=ps.eps, n_leaf=16, soft_kind=0, precision=1)
+        f.build(x, m)
+        a, phi = f.accel()
+        g = native.KdFmm(theta=0.5, eps=ps.eps, n_leaf=16, soft_kind=0, precision=1)
+        g.build(x, m)
+        a2, phi2 = g.accel()
+        torch.cuda.synchronize()
+        e1, e2 = f.export(lists=True), g.export(lists=True)
+        assert np.array_equal(e1.perm, e2.perm)
+        assert np.array_equal(e1.cell_ints, e2.cell_ints)
+        assert np.array_equal(e1.cell_reals, e2.cell_reals)
+        assert np.array_equal(e1.near_idx, e2.near_idx) and np.array_equal(e1.far_idx, e2.far_idx)
+        assert torch.equal(a, a2) and torch.equal(phi, phi2)
+        assert f.stats()["ncells"] == g.stats()["ncells"]
