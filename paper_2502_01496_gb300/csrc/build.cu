@@ -17,6 +17,7 @@
 // Then the cells are renumbered in pre-order from their particle ranges, the
 // quadrupoles and h_max are accumulated bottom-up, and float32 views for the
 // walk, the M2L and the P2P are derived.
+#include <algorithm>
 #include <climits>
 
 #include "kdfmm_internal.cuh"
@@ -1476,7 +1477,10 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
   }
   cudaMemsetAsync(t->c.ready, 0,
                   (size_t)(deferred ? t->cap_cells : (int64_t)t->ncells) * sizeof(int32_t), s);
-  k_upward<<<kGridBlocks / 2, 128, 0, s>>>(t->c, t->leaf_cells, t->counters, t->tp);
+  // one thread per leaf (the climb is latency-bound): the grid follows the last
+  // known leaf count with a margin; more leaves than threads loop
+  const int64_t up_threads = std::max<int64_t>(t->nleaves, 1) + t->nleaves / 4 + 128;
+  k_upward<<<blocks_for(up_threads, 128), 128, 0, s>>>(t->c, t->leaf_cells, t->counters, t->tp);
   k_derive_cells<<<kGridBlocks, 256, 0, s>>>(t->c, t->counters, t->com_bound);
   k_particles32<<<kGridBlocks, 256, 0, s>>>(t->c, t->leaf_cells, t->counters, t->tp, t->pf, t->ph);
   t->launches += 15;

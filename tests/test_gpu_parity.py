@@ -197,3 +197,36 @@ def test_rebuilds_match_fresh_handles(oracle):
         assert np.array_equal(e1.near_idx, e2.near_idx) and np.array_equal(e1.far_idx, e2.far_idx)
         assert torch.equal(a, a2) and torch.equal(phi, phi2)
         assert f.stats()["ncells"] == g.stats()["ncells"]
+
+
+@pytest.mark.slow
+def test_large_clumpy_evaluation_sampled(oracle):
+    """The large single evaluation: 2^24 particles, half uniform in the unit
+    cube and half in 64 Gaussian clumps, masses log-uniform over a decade,
+    eps 1e-3, theta 0.5, leaves of at most 32, mixed precision.  The whole tree
+    (particle order, every cell's structure, M, centre of mass, s, h_max, Q)
+    against the oracle's; forces of 100 random leaves against the oracle's
+    evaluation of those leaves."""
+    import torch
+    from paper_2502_01496_gb300 import native
+    ps = W.uniform_clumps(1 << 24, W.seed_for(2))
+    x = torch.tensor(ps.x, device="cuda")
+    m = torch.tensor(ps.m, device="cuda")
+    f = native.KdFmm(theta=0.5, eps=ps.eps, n_leaf=32, soft_kind=0, precision=1)
+    f.build(x, m)
+    a, phi = f.accel()
+    torch.cuda.synchronize()
+    ga, gphi = a.cpu().numpy(), phi.cpu().numpy()
+    assert np.isfinite(ga).all() and np.isfinite(gphi).all()
+    ex = f.export(lists=False)
+    del a, phi, x, m
+    T = oracle.Tree(ps.x, ps.m, None, theta=0.5, n_leaf=32, soft_kind=0, eps=ps.eps)
+    assert_tree_bit_exact({"ex": ex}, {"order": T.order(), "cells": T.cells()})
+    rng = np.random.default_rng(11)
+    leaf_ids = ex.leaf_ids
+    leaves = np.sort(rng.choice(leaf_ids, 100, replace=False))
+    oa, ophi = T.eval(leaves=leaves)
+    rows = np.nonzero(np.isfinite(oa[:, 0]))[0]
+    ea, ep = rel_errors(ga, gphi, oa, ophi, rows)
+    assert rows.size > 100
+    assert ea.max() < 2e-5 and ep.max() < 2e-5, (ea.max(), ep.max())
