@@ -54,6 +54,15 @@ extern "C" {
 
 typedef struct kdfmm_tree_s* kdfmm_tree;   /* opaque, library-owned */
 
+/* Far-field expansion.  PHANTOM: Eq. 6 and its first and second derivatives at
+ * full order (Eq. 8; the quadrupole reaches the Hessian term, 1/r^6).
+ * STANDARD: the standard p = 3 Cartesian series of the multipole section
+ * (octupoles dropped; sink and source orders add up to at most p - 1 = 2 in
+ * the acceleration), i.e. the quadrupole enters the acceleration at order 0
+ * only (highest power of 1/r: 4).  The walk is the same leaf-only walk. */
+#define KDFMM_EXPANSION_PHANTOM 0
+#define KDFMM_EXPANSION_STANDARD 1
+
 typedef struct {
     double theta;        /* opening parameter of Eq. 4, 0 <= theta <= 1 */
     double eps;          /* Plummer softening length (soft_kind 0); also h_i then */
@@ -61,7 +70,7 @@ typedef struct {
     int32_t n_leaf;      /* a cell holding more particles is split (Sec. 2); 1..32 */
     int32_t soft_kind;   /* KDFMM_SOFT_PLUMMER or KDFMM_SOFT_M4 */
     int32_t precision;   /* KDFMM_FP64 or KDFMM_MIXED */
-    int32_t reserved;    /* must be 0 */
+    int32_t expansion;   /* KDFMM_EXPANSION_PHANTOM (0) or KDFMM_EXPANSION_STANDARD (1) */
 } kdfmm_params;
 
 /* Statistics of the last build / evaluation (kdfmm_tree_stats indices). */

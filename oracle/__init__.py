@@ -24,6 +24,8 @@ _LIB = os.path.join(_HERE, "libkdfmm_oracle.so")
 
 SOFT_PLUMMER = 0
 SOFT_M4 = 1
+EXP_PHANTOM = 0    # Eq. 6 expanded to full order in the sink displacement
+EXP_STANDARD = 1   # standard p = 3 Cartesian series (orders of sink and source add to <= 2)
 
 _lib = None
 
@@ -47,7 +49,7 @@ def _load():
     P = ctypes.c_void_p
     i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     L.orc_build.restype = P
-    L.orc_build.argtypes = [i64, P, P, P, f64, i32, i32, f64, f64]
+    L.orc_build.argtypes = [i64, P, P, P, f64, i32, i32, f64, f64, i32]
     L.orc_free.argtypes = [P]
     for name in ("orc_ncells", "orc_nleaves", "orc_maxdepth", "orc_nfallback"):
         getattr(L, name).restype = i32
@@ -74,7 +76,7 @@ def _load():
     L.orc_monomials.restype = i32
     L.orc_monomials.argtypes = [P]
     L.orc_moments.argtypes = [i64, P, P, P, P, P, P]
-    L.orc_m2l.argtypes = [P, f64, P, P, P]
+    L.orc_m2l.argtypes = [P, f64, P, i32, P, P]
     L.orc_l2p.argtypes = [P, P, P, P, P]
     L.orc_acc_node.argtypes = [P, f64, P, P]
     L.orc_pair.argtypes = [P, f64, f64, f64, i32, f64, P, P]
@@ -130,7 +132,7 @@ class Tree:
     """kd-tree built by the oracle (Sec. 2) for one particle set."""
 
     def __init__(self, x, m, h=None, *, theta=0.5, n_leaf=16, soft_kind=SOFT_PLUMMER,
-                 eps=0.01, r_kern=2.0):
+                 eps=0.01, r_kern=2.0, expansion=EXP_PHANTOM):
         L = _load()
         self.x = _f64(x, (-1, 3))
         self.n = self.x.shape[0]
@@ -138,8 +140,9 @@ class Tree:
         self.h = None if h is None else _f64(h)
         self.theta, self.n_leaf, self.soft_kind = float(theta), int(n_leaf), int(soft_kind)
         self.eps, self.r_kern = float(eps), float(r_kern)
+        self.expansion = int(expansion)
         self._t = L.orc_build(self.n, _p(self.x), _p(self.m), _p(self.h), self.theta,
-                              self.n_leaf, self.soft_kind, self.eps, self.r_kern)
+                              self.n_leaf, self.soft_kind, self.eps, self.r_kern, self.expansion)
         if not self._t:
             raise ValueError("oracle build rejected the arguments")
 
@@ -283,12 +286,13 @@ def moments(x, m):
     return float(M[0]), com, Q, float(s[0])
 
 
-def m2l(r, M, Q):
+def m2l(r, M, Q, expansion=EXP_PHANTOM):
     """Local-expansion Taylor coefficients of one source about r: potential (20,)
-    and acceleration (3, 20) -- Eq. 6 and its derivatives."""
+    and acceleration (3, 20) -- Eq. 6 and its derivatives (or the standard p = 3
+    series with expansion=EXP_STANDARD)."""
     r, Q = _f64(r), _f64(Q)
     pot, acc = np.zeros(20), np.zeros(60)
-    _load().orc_m2l(_p(r), float(M), _p(Q), _p(pot), _p(acc))
+    _load().orc_m2l(_p(r), float(M), _p(Q), int(expansion), _p(pot), _p(acc))
     return pot, acc.reshape(3, 20)
 
 

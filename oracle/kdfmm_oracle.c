@@ -22,7 +22,9 @@
  *      partner (Sec. 2, Sec. 4).
  *   4. M2L: the acceleration field of beta about r = com_alpha - com_beta, Eq. 6,
  *      and its first and second derivatives (a forward-mode Taylor "jet"
- *      evaluation of Eq. 6 exactly as printed).
+ *      evaluation of Eq. 6 exactly as printed).  Optionally the standard p = 3
+ *      Cartesian series of the multipole section instead (sink and source
+ *      orders add up to at most 2: the quadrupole only at order 0).
  *   5. L2P: second-order Taylor expansion of that field at each particle, Eq. 8.
  *   6. P2P: softened direct summation over the particles of opened leaves,
  *      Plummer softening or the symmetrised M4-kernel Green's function (Eq. 13,
@@ -185,13 +187,40 @@ static jet jet_pot_node(const double r[3], double M, const double Q[6]) {
 /* Local expansion of one leaf: Taylor coefficients about its centre of mass. */
 typedef struct { double pot[JN]; double acc[3][JN]; } local_exp;
 
-static void local_add_m2l(local_exp* L, const double r[3], double M, const double Q[6]) {
-    jet acc[3];
-    jet_acc_node(r, M, Q, acc);
-    jet pot = jet_pot_node(r, M, Q);
+enum { EXP_PHANTOM = 0, EXP_STANDARD = 1 };
+
+static int mono_order(int k) { return g_mono[k][0] + g_mono[k][1] + g_mono[k][2]; }
+
+/* expansion EXP_PHANTOM: Eq. 6 and its potential expanded to full order in
+ * the sink displacement x (the quadrupole reaches the Hessian term, 1/r^6).
+ * expansion EXP_STANDARD: the standard p = 3 Cartesian series (the multipole
+ * section's series with p = 3 and no octupole): sink and source orders add up to
+ * at most p - 1 = 2 for the acceleration and p = 3 for the potential, so the
+ * monopole enters at every order but the quadrupole (source order 2) only at
+ * order 0 of the acceleration and orders <= 1 of the potential (highest power
+ * of 1/r: 4).  Both parts are linear in (M, Q), taken separately here. */
+static void local_add_m2l(local_exp* L, const double r[3], double M, const double Q[6],
+                          int expansion) {
+    static const double Q0[6] = {0, 0, 0, 0, 0, 0};
+    if (expansion == EXP_PHANTOM) {
+        jet acc[3];
+        jet_acc_node(r, M, Q, acc);
+        jet pot = jet_pot_node(r, M, Q);
+        for (int k = 0; k < JN; ++k) {
+            L->pot[k] += pot.c[k];
+            for (int i = 0; i < 3; ++i) L->acc[i][k] += acc[i].c[k];
+        }
+        return;
+    }
+    jet accm[3], accq[3];
+    jet_acc_node(r, M, Q0, accm);
+    jet_acc_node(r, 0.0, Q, accq);
+    jet potm = jet_pot_node(r, M, Q0);
+    jet potq = jet_pot_node(r, 0.0, Q);
     for (int k = 0; k < JN; ++k) {
-        L->pot[k] += pot.c[k];
-        for (int i = 0; i < 3; ++i) L->acc[i][k] += acc[i].c[k];
+        const int o = mono_order(k);
+        L->pot[k] += potm.c[k] + (o <= 1 ? potq.c[k] : 0.0);
+        for (int i = 0; i < 3; ++i) L->acc[i][k] += accm[i].c[k] + (o == 0 ? accq[i].c[k] : 0.0);
     }
 }
 
@@ -290,7 +319,7 @@ typedef struct {
 
 typedef struct {
     int64_t n;
-    int32_t n_leaf, soft_kind;
+    int32_t n_leaf, soft_kind, expansion;
     double theta, eps, r_kern;
     double *x, *m, *h;               /* copies, caller order */
     int64_t* order;                  /* tree position -> caller index */
@@ -420,12 +449,12 @@ static int32_t build_cell(otree* T, int64_t first, int64_t n, int32_t parent, in
 }
 
 otree* orc_build(int64_t n, const double* x, const double* m, const double* h, double theta,
-                 int32_t n_leaf, int32_t soft_kind, double eps, double r_kern) {
-    if (n <= 0 || n_leaf < 1) return NULL;
+                 int32_t n_leaf, int32_t soft_kind, double eps, double r_kern, int32_t expansion) {
+    if (n <= 0 || n_leaf < 1 || (expansion != EXP_PHANTOM && expansion != EXP_STANDARD)) return NULL;
     jet_init();
     otree* T = (otree*)calloc(1, sizeof(otree));
     T->n = n; T->n_leaf = n_leaf; T->soft_kind = soft_kind;
-    T->theta = theta; T->eps = eps; T->r_kern = r_kern;
+    T->theta = theta; T->eps = eps; T->r_kern = r_kern; T->expansion = expansion;
     T->x = (double*)malloc(sizeof(double) * 3 * (size_t)n);
     T->m = (double*)malloc(sizeof(double) * (size_t)n);
     T->h = (double*)malloc(sizeof(double) * (size_t)n);
@@ -582,7 +611,7 @@ static void eval_leaf(const otree* T, int32_t alpha, const int32_t* far, int64_t
     for (int64_t f = 0; f < nfar; ++f) {
         const ocell* cb = &T->cells[far[f]];
         double r[3] = {ca->com[0] - cb->com[0], ca->com[1] - cb->com[1], ca->com[2] - cb->com[2]};
-        local_add_m2l(&L, r, cb->M, cb->Q);
+        local_add_m2l(&L, r, cb->M, cb->Q, T->expansion);
     }
     for (int64_t k = 0; k < ca->count; ++k) {
         int64_t i = T->order[ca->first + k];
@@ -784,11 +813,12 @@ void orc_moments(int64_t n, const double* x, const double* m, double* M, double*
 /* Local expansion coefficients of one source (M, Q) about r: 20 potential
  * coefficients and 3 x 20 acceleration coefficients (orders <= 3; Eq. 8 uses
  * orders <= 2). */
-void orc_m2l(const double* r, double M, const double* Q, double* pot, double* acc) {
+void orc_m2l(const double* r, double M, const double* Q, int32_t expansion, double* pot,
+             double* acc) {
     jet_init();
     local_exp L;
     memset(&L, 0, sizeof L);
-    local_add_m2l(&L, r, M, Q);
+    local_add_m2l(&L, r, M, Q, expansion);
     memcpy(pot, L.pot, sizeof L.pot);
     for (int i = 0; i < 3; ++i) memcpy(acc + JN * i, L.acc[i], sizeof(double) * JN);
 }

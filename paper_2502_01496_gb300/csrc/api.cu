@@ -44,7 +44,8 @@ int check_params(const kdfmm_params* p, const double* h) {
     return set_error(KDFMM_ERR_INVALID_ARG, "eps must be finite and >= 0");
   if (!(std::isfinite(p->r_kern) && p->r_kern >= 0.0))
     return set_error(KDFMM_ERR_INVALID_ARG, "r_kern must be finite and >= 0");
-  if (p->reserved != 0) return set_error(KDFMM_ERR_INVALID_ARG, "reserved must be 0");
+  if (p->expansion != KDFMM_EXPANSION_PHANTOM && p->expansion != KDFMM_EXPANSION_STANDARD)
+    return set_error(KDFMM_ERR_INVALID_ARG, "unknown expansion %d", p->expansion);
   if (p->soft_kind == KDFMM_SOFT_M4 && h == nullptr)
     return set_error(KDFMM_ERR_INVALID_ARG, "M4 kernel softening needs smoothing lengths h");
   return KDFMM_OK;

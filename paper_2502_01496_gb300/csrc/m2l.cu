@@ -16,6 +16,10 @@
 //         + t3 (R_a Q_bc + R_b Q_ac + R_c Q_ab + d_ab u_c + d_ac u_b + d_bc u_a)
 // with s_n = -M g_n - g_(n+2) q / 6 and t_n = -g_n / 3.
 //
+// The standard p = 3 series (sink and source orders adding up to at most 2 in
+// the acceleration, the multipole section of the paper) differs only in
+// dropping the quadrupole's C2 and C3 terms (template flag STD).
+//
 // One warp per sink leaf; its lanes take the far cells in turn.  Mixed mode
 // works in float32 with the centre-of-mass difference formed from
 // (high, low) float pairs and compensated sums for C0 and C1; FP64 mode works
@@ -56,7 +60,10 @@ __device__ __forceinline__ T c3e(int a, int b, int c, const T R[3], const T u[3]
 
 // Local coefficients of one source: out[0] C0; [1..3] C1 x y z; [4..9] C2 xx
 // xy xz yy yz zz; [10..19] C3 xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz.
-template <class T>
+// STD: the standard p = 3 series (sink and source orders add up to at most
+// p - 1 = 2 for the acceleration): the quadrupole keeps only its C0 and C1
+// terms, C2 and C3 come from the monopole alone.
+template <class T, bool STD = false>
 __device__ __forceinline__ void m2l_coeffs(T Rx, T Ry, T Rz, T M, const T Q[6], T out[20]) {
   const T R[3] = {Rx, Ry, Rz};
   const T Qm[3][3] = {{Q[0], Q[1], Q[2]}, {Q[1], Q[3], Q[4]}, {Q[2], Q[4], Q[5]}};
@@ -75,18 +82,22 @@ __device__ __forceinline__ void m2l_coeffs(T Rx, T Ry, T Rz, T M, const T Q[6], 
   const T sixth = T(1) / T(6), third = T(1) / T(3);
   const T qs = q * sixth;
   const T s1 = -M * g1 - g3 * qs;
-  const T s2 = -M * g2 - g4 * qs;
-  const T s3 = -M * g3 - g5 * qs;
-  const T t2 = -g2 * third, t3 = -g3 * third, t4 = -g4 * third;
+  const T t2 = -g2 * third;
   out[0] = -M * g0 - g2 * qs;
 #pragma unroll
   for (int i = 0; i < 3; ++i) out[1 + i] = s1 * R[i] + t2 * u[i];
-  out[4] = c2e<T>(0, 0, R, u, Qm, s1, s2, t2, t3);
-  out[5] = c2e<T>(0, 1, R, u, Qm, s1, s2, t2, t3);
-  out[6] = c2e<T>(0, 2, R, u, Qm, s1, s2, t2, t3);
-  out[7] = c2e<T>(1, 1, R, u, Qm, s1, s2, t2, t3);
-  out[8] = c2e<T>(1, 2, R, u, Qm, s1, s2, t2, t3);
-  out[9] = c2e<T>(2, 2, R, u, Qm, s1, s2, t2, t3);
+  // second and third order: both parts, or the monopole alone (STD)
+  const T s1h = STD ? -M * g1 : s1;
+  const T s2 = STD ? -M * g2 : -M * g2 - g4 * qs;
+  const T s3 = STD ? -M * g3 : -M * g3 - g5 * qs;
+  const T t2h = STD ? T(0) : t2;
+  const T t3 = STD ? T(0) : -g3 * third, t4 = STD ? T(0) : -g4 * third;
+  out[4] = c2e<T>(0, 0, R, u, Qm, s1h, s2, t2h, t3);
+  out[5] = c2e<T>(0, 1, R, u, Qm, s1h, s2, t2h, t3);
+  out[6] = c2e<T>(0, 2, R, u, Qm, s1h, s2, t2h, t3);
+  out[7] = c2e<T>(1, 1, R, u, Qm, s1h, s2, t2h, t3);
+  out[8] = c2e<T>(1, 2, R, u, Qm, s1h, s2, t2h, t3);
+  out[9] = c2e<T>(2, 2, R, u, Qm, s1h, s2, t2h, t3);
   out[10] = c3e<T>(0, 0, 0, R, u, Qm, s2, s3, t3, t4);
   out[11] = c3e<T>(0, 0, 1, R, u, Qm, s2, s3, t3, t4);
   out[12] = c3e<T>(0, 0, 2, R, u, Qm, s2, s3, t3, t4);
@@ -113,6 +124,7 @@ struct M2LArgs {
   double* lexp64;
 };
 
+template <bool STD>
 __global__ void __launch_bounds__(256) k_m2l_mixed(M2LArgs A) {
   const int lane = threadIdx.x & 31;
   const int nleaves = min(A.counters[C_LEAVES], A.max_leaves);
@@ -135,7 +147,7 @@ __global__ void __launch_bounds__(256) k_m2l_mixed(M2LArgs A) {
     const float Rz = (ah.z - b0.z) + (al.z - b1.z);
     const float Q[6] = {b2.x, b2.y, b2.z, b2.w, b3.x, b3.y};
     float C[20];
-    m2l_coeffs<float>(Rx, Ry, Rz, b0.w, Q, C);
+    m2l_coeffs<float, STD>(Rx, Ry, Rz, b0.w, Q, C);
 #pragma unroll
     for (int j = 0; j < 4; ++j) df_add(acc[j], lo[j], C[j]);
 #pragma unroll
@@ -167,6 +179,7 @@ __global__ void __launch_bounds__(256) k_m2l_mixed(M2LArgs A) {
   }
 }
 
+template <bool STD>
 __global__ void __launch_bounds__(256) k_m2l_fp64(M2LArgs A) {
   const int lane = threadIdx.x & 31;
   const int nleaves = min(A.counters[C_LEAVES], A.max_leaves);
@@ -183,7 +196,7 @@ __global__ void __launch_bounds__(256) k_m2l_fp64(M2LArgs A) {
     const int b = A.far_idx[off + e];
     const double* sb = A.src64 + 10 * (int64_t)b;
     double C[20];
-    m2l_coeffs<double>(ax - sb[0], ay - sb[1], az - sb[2], sb[3], sb + 4, C);
+    m2l_coeffs<double, STD>(ax - sb[0], ay - sb[1], az - sb[2], sb[3], sb + 4, C);
 #pragma unroll
     for (int j = 0; j < 20; ++j) acc[j] += C[j];
   }
@@ -220,8 +233,14 @@ int run_m2l(kdfmm_tree_s* t, cudaStream_t s) {
   A.lexp32 = t->lexp32;
   A.lexp64 = t->lexp64;
   const unsigned g = blocks_for((int64_t)std::max(t->grid_leaves, 1) * 32, 256);
-  if (t->p.precision == KDFMM_MIXED) k_m2l_mixed<<<g, 256, 0, s>>>(A);
-  else k_m2l_fp64<<<g, 256, 0, s>>>(A);
+  const bool std_exp = t->p.expansion == KDFMM_EXPANSION_STANDARD;
+  if (t->p.precision == KDFMM_MIXED) {
+    if (std_exp) k_m2l_mixed<true><<<g, 256, 0, s>>>(A);
+    else k_m2l_mixed<false><<<g, 256, 0, s>>>(A);
+  } else {
+    if (std_exp) k_m2l_fp64<true><<<g, 256, 0, s>>>(A);
+    else k_m2l_fp64<false><<<g, 256, 0, s>>>(A);
+  }
   t->launches += 1;
   return check_cuda(cudaGetLastError(), "m2l launch");
 }

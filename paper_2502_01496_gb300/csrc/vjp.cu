@@ -86,7 +86,9 @@ __device__ __forceinline__ T c3e(int a, int b, int c, const T R[3], const T u[3]
 // of the potential Phi = -M/R - Q_jk R_j R_k / (2 R^5) and its derivatives
 // (the closed forms of m2l.cu); contracting as each coefficient is formed
 // keeps one accumulator instead of twenty.
-template <class T>
+// STD: the standard p = 3 series -- the quadrupole keeps only its C0 and C1
+// terms (as in m2l.cu).
+template <class T, bool STD>
 __device__ T m2l_contract(const T R[3], double M, const double Q[6], const double w[20]) {
   const T Qm[3][3] = {{tc<T>(Q[0]), tc<T>(Q[1]), tc<T>(Q[2])},
                       {tc<T>(Q[1]), tc<T>(Q[3]), tc<T>(Q[4])},
@@ -105,15 +107,19 @@ __device__ T m2l_contract(const T R[3], double M, const double Q[6], const doubl
   const T qs = q * tc<T>(1.0 / 6.0);
   const T Mt = tc<T>(M);
   const T s1 = -(Mt * g1) - g3 * qs;
-  const T s2 = -(Mt * g2) - g4 * qs;
-  const T s3 = -(Mt * g3) - g5 * qs;
-  const T t2 = g2 * tc<T>(-1.0 / 3.0), t3 = g3 * tc<T>(-1.0 / 3.0), t4 = g4 * tc<T>(-1.0 / 3.0);
+  const T t2 = g2 * tc<T>(-1.0 / 3.0);
   T acc = tc<T>(w[0]) * (-(Mt * g0) - g2 * qs);
   for (int i = 0; i < 3; ++i) acc += tc<T>(w[1 + i]) * (s1 * R[i] + t2 * u[i]);
+  const T s1h = STD ? -(Mt * g1) : s1;
+  const T s2 = STD ? -(Mt * g2) : -(Mt * g2) - g4 * qs;
+  const T s3 = STD ? -(Mt * g3) : -(Mt * g3) - g5 * qs;
+  const T t2h = STD ? tc<T>(0.0) : t2;
+  const T t3 = STD ? tc<T>(0.0) : g3 * tc<T>(-1.0 / 3.0);
+  const T t4 = STD ? tc<T>(0.0) : g4 * tc<T>(-1.0 / 3.0);
   const int c2a[6] = {0, 0, 0, 1, 1, 2}, c2b[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
   for (int k = 0; k < 6; ++k)
-    acc += tc<T>(w[4 + k]) * c2e<T>(c2a[k], c2b[k], R, u, Qm, s1, s2, t2, t3);
+    acc += tc<T>(w[4 + k]) * c2e<T>(c2a[k], c2b[k], R, u, Qm, s1h, s2, t2h, t3);
   const int c3a[10] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 2}, c3b[10] = {0, 0, 0, 1, 1, 2, 1, 1, 2, 2},
             c3c[10] = {0, 1, 2, 1, 2, 2, 1, 2, 2, 2};
 #pragma unroll
@@ -247,6 +253,7 @@ __global__ void k_vjp_l2p(VjpArgs V) {
 }
 
 // M2L reverse: warp per sink leaf, lanes over its far cells.
+template <bool STD>
 __global__ void k_vjp_m2l(VjpArgs V) {
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -266,14 +273,14 @@ __global__ void k_vjp_m2l(VjpArgs V) {
     // r-derivatives of sum_j cb_j C_j by dual numbers; M and Q enter linearly
     const Dual3 R[3] = {Dual3{r[0], {1.0, 0.0, 0.0}}, Dual3{r[1], {0.0, 1.0, 0.0}},
                         Dual3{r[2], {0.0, 0.0, 1.0}}};
-    const Dual3 cr = m2l_contract<Dual3>(R, V.c.M[b], Qb, cb);
+    const Dual3 cr = m2l_contract<Dual3, STD>(R, V.c.M[b], Qb, cb);
     const double gr[3] = {cr.d[0], cr.d[1], cr.d[2]};
-    const double mbar = m2l_contract<double>(r, 1.0, zq, cb);
+    const double mbar = m2l_contract<double, STD>(r, 1.0, zq, cb);
     double qbar[6];
     for (int qq = 0; qq < 6; ++qq) {
       double eq[6] = {0, 0, 0, 0, 0, 0};
       eq[qq] = 1.0;
-      qbar[qq] = m2l_contract<double>(r, 0.0, eq, cb);
+      qbar[qq] = m2l_contract<double, STD>(r, 0.0, eq, cb);
     }
     rx += gr[0]; ry += gr[1]; rz += gr[2];
     double* cbb = V.cell_bar + 10 * (int64_t)b;
@@ -510,7 +517,10 @@ int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, 
   cudaMemsetAsync(V.cell_bar, 0, (size_t)nc * 10 * sizeof(double), s);
   k_gather_abar<<<blocks_for(n, 256), 256, 0, s>>>(a_bar, V);
   k_vjp_l2p<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
-  k_vjp_m2l<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
+  if (t->p.expansion == KDFMM_EXPANSION_STANDARD)
+    k_vjp_m2l<true><<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
+  else
+    k_vjp_m2l<false><<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
   k_vjp_p2p<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
   k_vjp_moments<<<blocks_for(nl, 128), 128, 0, s>>>(V);
   k_scatter_bar<<<blocks_for(n, 256), 256, 0, s>>>(V, x_bar, m_bar);

@@ -27,6 +27,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "CAPACITY
           -6: "NONFINITE", -7: "INTERNAL"}
 SOFT_PLUMMER, SOFT_M4 = 0, 1
 FP64, MIXED = 0, 1
+EXPANSION_PHANTOM, EXPANSION_STANDARD = 0, 1
 MAX_LEAF = 32
 STAT_NAMES = ("n", "ncells", "nleaves", "depth", "nfar", "nnear", "np2p", "nfallback", "nexact",
               "launches")
@@ -42,13 +43,15 @@ class KdfmmError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("eps", ctypes.c_double), ("r_kern", ctypes.c_double),
                 ("n_leaf", ctypes.c_int32), ("soft_kind", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("expansion", ctypes.c_int32)]
 
 
 def make_params(theta=0.5, eps=0.01, r_kern=2.0, n_leaf=16, soft_kind=SOFT_PLUMMER,
-                precision=MIXED) -> Params:
+                precision=MIXED, expansion=0) -> Params:
+    """expansion: 0 = Eq. 6 at full order (the paper's scheme), 1 = the standard
+    p = 3 Cartesian series."""
     return Params(float(theta), float(eps), float(r_kern), int(n_leaf), int(soft_kind),
-                  int(precision), 0)
+                  int(precision), int(expansion))
 
 
 _lib = None

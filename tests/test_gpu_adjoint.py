@@ -207,3 +207,35 @@ def test_vjp_invalid_args():
         f.vjp(ab[:5])
     with pytest.raises(TypeError):
         f.vjp(ab.float())
+
+
+def test_vjp_standard_expansion_against_oracle_differences(oracle):
+    """The adjoint of the standard p = 3 series (FP64) against Richardson
+    differences of the oracle's standard-series evaluation on frozen lists."""
+    import torch
+    from paper_2502_01496_gb300 import native
+    ps = W.plummer(1200, W.seed_for(0, 25))
+    n = ps.n
+    rng = np.random.default_rng(5)
+    ab = rng.standard_normal((n, 3))
+    f = native.KdFmm(theta=0.6, eps=ps.eps, n_leaf=16, soft_kind=0, precision=FP64, expansion=1)
+    f.build(_cuda(ps.x), _cuda(ps.m))
+    f.accel()
+    xb, mb = f.vjp(_cuda(ab))
+    torch.cuda.synchronize()
+    xb, mb = xb.cpu().numpy(), mb.cpu().numpy()
+    T = oracle.Tree(ps.x, ps.m, None, theta=0.6, n_leaf=16, soft_kind=0, eps=ps.eps, expansion=1)
+    L0 = T.walk()
+
+    def L(x, m):
+        T.moments_frozen(x, m, None)
+        a, _ = T.eval_lists(L0)
+        return float(np.sum(ab * a))
+
+    for _ in range(3):
+        dx = rng.standard_normal((n, 3))
+        dm = rng.standard_normal(n) * ps.m
+        fd = _richardson(L, ps.x, ps.m, dx, dm, 3e-5)
+        ad = float(np.sum(xb * dx) + np.sum(mb * dm))
+        scale = np.linalg.norm(xb) * np.linalg.norm(dx) + np.linalg.norm(mb) * np.linalg.norm(dm)
+        assert abs(fd - ad) <= 1e-8 * scale, (fd, ad)

@@ -230,3 +230,36 @@ def test_large_clumpy_evaluation_sampled(oracle):
     ea, ep = rel_errors(ga, gphi, oa, ophi, rows)
     assert rows.size > 100
     assert ea.max() < 2e-5 and ep.max() < 2e-5, (ea.max(), ep.max())
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", ["plummer", "polytrope_m4"])
+def test_standard_expansion_against_oracle(oracle, case, prec):
+    """The standard p = 3 series (expansion 1): same tree and lists; forces
+    against the oracle's standard series; the total force, still non-zero
+    under the leaf-only walk, within 1e-3 of the oracle's."""
+    import torch
+    from paper_2502_01496_gb300 import native
+    ps = (W.plummer(4096, W.seed_for(0, 40)) if case == "plummer"
+          else W.polytrope_binary(2048, W.seed_for(1, 41)))
+    f = native.KdFmm(theta=0.5, eps=ps.eps, n_leaf=16, soft_kind=ps.soft_kind, precision=prec,
+                     expansion=1)
+    x = torch.tensor(ps.x, device="cuda")
+    m = torch.tensor(ps.m, device="cuda")
+    h = None if ps.h is None else torch.tensor(ps.h, device="cuda")
+    f.build(x, m, h)
+    a, phi = f.accel()
+    torch.cuda.synchronize()
+    ga, gphi = a.cpu().numpy(), phi.cpu().numpy()
+    T = oracle.Tree(ps.x, ps.m, ps.h, theta=0.5, n_leaf=16, soft_kind=ps.soft_kind, eps=ps.eps,
+                    expansion=1)
+    oa, ophi = T.eval()
+    assert_lists_bit_exact({"ex": f.export(lists=True)}, {"lists": T.walk()})
+    ea, ep = rel_errors(ga, gphi, oa, ophi)
+    tol = 1e-12 if prec == 0 else 2e-5
+    assert ea.max() < tol and ep.max() < tol, (ea.max(), ep.max())
+    Fg, Fo = fsum_force(ps.m, ga), fsum_force(ps.m, oa)
+    assert np.linalg.norm(Fg - Fo) <= 1e-3 * np.linalg.norm(Fo)
+    T0 = oracle.Tree(ps.x, ps.m, ps.h, theta=0.5, n_leaf=16, soft_kind=ps.soft_kind, eps=ps.eps)
+    a0, _ = T0.eval()
+    assert np.linalg.norm(Fo - fsum_force(ps.m, a0)) > 1e-3 * np.linalg.norm(Fo)
