@@ -76,6 +76,18 @@ def _load():
     L.orc_monomials.restype = i32
     L.orc_monomials.argtypes = [P]
     L.orc_moments.argtypes = [i64, P, P, P, P, P, P]
+    L.orc_dual_walk.restype = P
+    L.orc_dual_walk.argtypes = [P]
+    L.orc_dual_nfar.restype = i64
+    L.orc_dual_nfar.argtypes = [P]
+    L.orc_dual_nnear.restype = i64
+    L.orc_dual_nnear.argtypes = [P]
+    L.orc_dual_get.argtypes = [P, P, P, P, P]
+    L.orc_dual_get.restype = None
+    L.orc_dual_free.argtypes = [P]
+    L.orc_dual_free.restype = None
+    L.orc_eval_dual.restype = i32
+    L.orc_eval_dual.argtypes = [P, P, P, P]
     L.orc_m2l.argtypes = [P, f64, P, i32, P, P]
     L.orc_l2p.argtypes = [P, P, P, P, P]
     L.orc_acc_node.argtypes = [P, f64, P, P]
@@ -126,6 +138,15 @@ class Lists:
     near_off: np.ndarray
     near_idx: np.ndarray
     ancestor_far: int
+
+
+@dataclass
+class DualLists:
+    """Symmetric dual-tree walk: far lists per cell, near lists per leaf."""
+    far_off: np.ndarray
+    far_idx: np.ndarray
+    near_off: np.ndarray
+    near_idx: np.ndarray
 
 
 class Tree:
@@ -224,6 +245,38 @@ class Tree:
                                 phi_long=extra[3], n_p2p=int(stats[0]), n_m2l=int(stats[1]))
         return a, phi
 
+
+    def dual_walk(self) -> "DualLists":
+        """Lists of the symmetric dual-tree walk: far list of every cell (ids in
+        ascending order), near list of every leaf (leaves in ascending id)."""
+        L = _load()
+        h = L.orc_dual_walk(self._t)
+        try:
+            nc, nl = self.ncells, self.nleaves
+            nf, nn = L.orc_dual_nfar(h), L.orc_dual_nnear(h)
+            far_off = np.empty(nc + 1, dtype=np.int64)
+            near_off = np.empty(nl + 1, dtype=np.int64)
+            far_idx = np.empty(max(nf, 1), dtype=np.int32)
+            near_idx = np.empty(max(nn, 1), dtype=np.int32)
+            L.orc_dual_get(h, _p(far_off), _p(far_idx), _p(near_off), _p(near_idx))
+            res = DualLists(far_off, far_idx[:nf], near_off, near_idx[:nn])
+        finally:
+            L.orc_dual_free(h)
+        return res
+
+    def eval_dual(self):
+        """a, phi (caller order) from the symmetric dual-tree walk."""
+        L = _load()
+        h = L.orc_dual_walk(self._t)
+        a = np.full((self.n, 3), np.nan)
+        phi = np.full(self.n, np.nan)
+        try:
+            rc = L.orc_eval_dual(self._t, h, _p(a), _p(phi))
+        finally:
+            L.orc_dual_free(h)
+        if rc != 0:
+            raise ValueError(f"oracle eval_dual failed ({rc})")
+        return a, phi
 
     def moments_frozen(self, x, m, h=None):
         """New positions / masses / smoothing lengths for the same particles,

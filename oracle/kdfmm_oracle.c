@@ -855,3 +855,191 @@ void orc_m4(double q, double* w, double* F, double* P) {
     *F = m4_F(q);
     *P = m4_P(q);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Symmetric dual-tree walk (the correction the paper's conclusions call for, */
+/* after Dehnen 2000/2002): cells interact in pairs, both ways, so that the   */
+/* expansions' Newton's third law for mutually interacting cells (Sec. 3)     */
+/* carries over to the whole system.  Not the paper's scheme; a separate mode. */
+/* ------------------------------------------------------------------------ */
+
+/* Two distinct cells are well separated when theta r > s_A + s_B (Eq. 4 made
+ * symmetric: both sizes) and their smoothing spheres cannot intersect
+ * (Eq. 5 not satisfied: r >= s_A + s_B + R_kern max(h_A, h_B)).  theta = 0
+ * separates nothing. */
+static int well_separated(const otree* T, const ocell* a, const ocell* b) {
+    if (T->theta == 0.0) return 0;
+    double dx = a->com[0] - b->com[0];
+    double dy = a->com[1] - b->com[1];
+    double dz = a->com[2] - b->com[2];
+    double r2 = dx * dx + dy * dy + dz * dz;
+    double ss = a->s + b->s;
+    if (!(T->theta * T->theta * r2 > ss * ss)) return 0;
+    double hm = a->hmax > b->hmax ? a->hmax : b->hmax;
+    double rr = ss + T->r_kern * hm;
+    return r2 >= rr * rr;
+}
+
+typedef struct { ivec a, b; } pairs;
+static void pairs_push(pairs* p, int32_t a, int32_t b) { ivec_push(&p->a, a); ivec_push(&p->b, b); }
+
+/* interact(A, B): a cell with itself splits into its children's pairs; a
+ * well-separated pair is a far (M2L) pair; two leaves that are not are a near
+ * (P2P) pair; otherwise the larger cell (by s; a leaf is never split; ties
+ * split A) is split. */
+static void dual_rec(const otree* T, int32_t A, int32_t B, pairs* far, pairs* near) {
+    const ocell* a = &T->cells[A];
+    const ocell* b = &T->cells[B];
+    if (A == B) {
+        if (a->left < 0) { pairs_push(near, A, A); return; }
+        dual_rec(T, a->left, a->left, far, near);
+        dual_rec(T, a->right, a->right, far, near);
+        dual_rec(T, a->left, a->right, far, near);
+        return;
+    }
+    if (well_separated(T, a, b)) { pairs_push(far, A, B); return; }
+    if (a->left < 0 && b->left < 0) { pairs_push(near, A, B); return; }
+    int split_a = a->left >= 0 && (b->left < 0 || a->s >= b->s);
+    if (split_a) {
+        dual_rec(T, a->left, B, far, near);
+        dual_rec(T, a->right, B, far, near);
+    } else {
+        dual_rec(T, A, b->left, far, near);
+        dual_rec(T, A, b->right, far, near);
+    }
+}
+
+/* Lists of the dual walk: far list of every cell (the cells it receives M2L
+ * from), near list of every leaf (the leaves it receives P2P from, itself
+ * included once); entries in ascending id. */
+typedef struct {
+    int32_t ncells, nleaves;
+    int64_t *far_off, *near_off;     /* ncells + 1, nleaves + 1 */
+    int32_t *far_idx, *near_idx;
+    int64_t nfar, nnear;
+} odual;
+
+static int cmp_i32(const void* x, const void* y) {
+    int32_t a = *(const int32_t*)x, b = *(const int32_t*)y;
+    return (a > b) - (a < b);
+}
+
+static void to_csr(int32_t nrows, const int32_t* rows, const int32_t* cols, int64_t n,
+                   int64_t** off_out, int32_t** idx_out) {
+    int64_t* off = (int64_t*)calloc((size_t)nrows + 1, sizeof(int64_t));
+    for (int64_t e = 0; e < n; ++e) off[rows[e] + 1]++;
+    for (int32_t r = 0; r < nrows; ++r) off[r + 1] += off[r];
+    int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * ((size_t)nrows + 1));
+    memcpy(cur, off, sizeof(int64_t) * ((size_t)nrows + 1));
+    for (int64_t e = 0; e < n; ++e) idx[cur[rows[e]]++] = cols[e];
+    for (int32_t r = 0; r < nrows; ++r)
+        qsort(idx + off[r], (size_t)(off[r + 1] - off[r]), sizeof(int32_t), cmp_i32);
+    free(cur);
+    *off_out = off;
+    *idx_out = idx;
+}
+
+odual* orc_dual_walk(const otree* T) {
+    pairs far = {{0}, {0}}, near = {{0}, {0}};
+    dual_rec(T, 0, 0, &far, &near);
+    /* far pairs act both ways; near pairs both ways, a leaf with itself once */
+    int64_t nf = 2 * far.a.n, nn = 0;
+    int32_t* fr = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nf > 0 ? nf : 1));
+    int32_t* fc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nf > 0 ? nf : 1));
+    for (int64_t e = 0; e < far.a.n; ++e) {
+        fr[2 * e] = far.a.v[e]; fc[2 * e] = far.b.v[e];
+        fr[2 * e + 1] = far.b.v[e]; fc[2 * e + 1] = far.a.v[e];
+    }
+    int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * (size_t)T->ncells);
+    int32_t nl = 0;
+    for (int32_t c = 0; c < T->ncells; ++c) rank[c] = T->cells[c].left < 0 ? nl++ : -1;
+    int32_t* nr = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * near.a.n + 1));
+    int32_t* nc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * near.a.n + 1));
+    for (int64_t e = 0; e < near.a.n; ++e) {
+        int32_t A = near.a.v[e], B = near.b.v[e];
+        nr[nn] = rank[A]; nc[nn] = B; ++nn;
+        if (A != B) { nr[nn] = rank[B]; nc[nn] = A; ++nn; }
+    }
+    odual* D = (odual*)calloc(1, sizeof(odual));
+    D->ncells = T->ncells;
+    D->nleaves = nl;
+    D->nfar = nf;
+    D->nnear = nn;
+    to_csr(T->ncells, fr, fc, nf, &D->far_off, &D->far_idx);
+    to_csr(nl, nr, nc, nn, &D->near_off, &D->near_idx);
+    free(fr); free(fc); free(nr); free(nc); free(rank);
+    free(far.a.v); free(far.b.v); free(near.a.v); free(near.b.v);
+    return D;
+}
+int64_t orc_dual_nfar(const odual* D) { return D->nfar; }
+int64_t orc_dual_nnear(const odual* D) { return D->nnear; }
+void orc_dual_get(const odual* D, int64_t* far_off, int32_t* far_idx, int64_t* near_off,
+                  int32_t* near_idx) {
+    memcpy(far_off, D->far_off, sizeof(int64_t) * ((size_t)D->ncells + 1));
+    memcpy(near_off, D->near_off, sizeof(int64_t) * ((size_t)D->nleaves + 1));
+    if (D->nfar) memcpy(far_idx, D->far_idx, sizeof(int32_t) * (size_t)D->nfar);
+    if (D->nnear) memcpy(near_idx, D->near_idx, sizeof(int32_t) * (size_t)D->nnear);
+}
+void orc_dual_free(odual* D) {
+    if (!D) return;
+    free(D->far_off); free(D->near_off); free(D->far_idx); free(D->near_idx);
+    free(D);
+}
+
+/* Forces from the dual walk's lists: every cell's local expansion from its
+ * far list (M2L, Eq. 6 or the standard series); at each particle the sum of
+ * the expansions of all cells that contain it, each evaluated about its own
+ * centre of mass (Eq. 8); plus the softened pair sums over the leaf's near
+ * list (j != i). */
+int32_t orc_eval_dual(const otree* T, const odual* D, double* a, double* phi) {
+    jet_init();
+    local_exp* L = (local_exp*)calloc((size_t)T->ncells, sizeof(local_exp));
+    if (!L) return -1;
+    for (int32_t c = 0; c < T->ncells; ++c) {
+        const ocell* ca = &T->cells[c];
+        for (int64_t e = D->far_off[c]; e < D->far_off[c + 1]; ++e) {
+            const ocell* cb = &T->cells[D->far_idx[e]];
+            double r[3] = {ca->com[0] - cb->com[0], ca->com[1] - cb->com[1],
+                           ca->com[2] - cb->com[2]};
+            local_add_m2l(&L[c], r, cb->M, cb->Q, T->expansion);
+        }
+    }
+    int32_t k = 0;
+    for (int32_t alpha = 0; alpha < T->ncells; ++alpha) {
+        const ocell* ca = &T->cells[alpha];
+        if (ca->left >= 0) continue;
+        for (int64_t q = 0; q < ca->count; ++q) {
+            int64_t i = T->order[ca->first + q];
+            const double* xi = &T->x[3 * i];
+            double as[3] = {0, 0, 0}, ps = 0.0;
+            for (int64_t e = D->near_off[k]; e < D->near_off[k + 1]; ++e) {
+                const ocell* cb = &T->cells[D->near_idx[e]];
+                for (int64_t u = 0; u < cb->count; ++u) {
+                    int64_t j = T->order[cb->first + u];
+                    if (j == i) continue;
+                    const double* xj = &T->x[3 * j];
+                    double d[3] = {xi[0] - xj[0], xi[1] - xj[1], xi[2] - xj[2]};
+                    double aij[3], pij;
+                    pair_interaction(d, T->m[j], T->h[i], T->h[j], T->soft_kind, T->eps, aij, &pij);
+                    as[0] += aij[0]; as[1] += aij[1]; as[2] += aij[2];
+                    ps += pij;
+                }
+            }
+            double al[3] = {0, 0, 0}, pl = 0.0;
+            for (int32_t c = alpha; c >= 0; c = T->cells[c].parent) {
+                const ocell* cc = &T->cells[c];
+                double xrel[3] = {xi[0] - cc->com[0], xi[1] - cc->com[1], xi[2] - cc->com[2]};
+                double ac[3], pc;
+                local_eval(&L[c], xrel, ac, &pc);
+                al[0] += ac[0]; al[1] += ac[1]; al[2] += ac[2];
+                pl += pc;
+            }
+            for (int d = 0; d < 3; ++d) a[3 * i + d] = as[d] + al[d];
+            if (phi) phi[i] = ps + pl;
+        }
+        ++k;
+    }
+    free(L);
+    return 0;
+}
