@@ -63,6 +63,17 @@ typedef struct kdfmm_tree_s* kdfmm_tree;   /* opaque, library-owned */
 #define KDFMM_EXPANSION_PHANTOM 0
 #define KDFMM_EXPANSION_STANDARD 1
 
+/* Walk.  LEAF: the paper's scheme -- every leaf walks the tree, super-cells
+ * never do (Sec. 4), so interactions are one-sided and the total force does
+ * not vanish.  DUAL: the symmetric dual-tree walk the paper's conclusions
+ * point to (after Dehnen): cells interact in pairs, both ways -- M2L into both
+ * cells when theta r > s_A + s_B and the smoothing spheres cannot meet, P2P
+ * between the two leaves otherwise, else the larger cell splits -- and every
+ * cell's expansion is translated down to the leaves (L2L).  Not the paper's
+ * method; a separate mode.  The adjoint and captured graphs cover LEAF only. */
+#define KDFMM_WALK_LEAF 0
+#define KDFMM_WALK_DUAL 1
+
 typedef struct {
     double theta;        /* opening parameter of Eq. 4, 0 <= theta <= 1 */
     double eps;          /* Plummer softening length (soft_kind 0); also h_i then */
@@ -71,6 +82,8 @@ typedef struct {
     int32_t soft_kind;   /* KDFMM_SOFT_PLUMMER or KDFMM_SOFT_M4 */
     int32_t precision;   /* KDFMM_FP64 or KDFMM_MIXED */
     int32_t expansion;   /* KDFMM_EXPANSION_PHANTOM (0) or KDFMM_EXPANSION_STANDARD (1) */
+    int32_t walk;        /* KDFMM_WALK_LEAF (0) or KDFMM_WALK_DUAL (1) */
+    int32_t reserved;    /* must be 0 */
 } kdfmm_params;
 
 /* Statistics of the last build / evaluation (kdfmm_tree_stats indices). */
@@ -228,7 +241,9 @@ int kdfmm_tree_stats(kdfmm_tree t, int64_t* stats);
  * cell_reals (ncells x 12 double: M, com x y z, s, h_max, Q xx xy xz yy yz zz);
  * leaf_ids (nleaves int32, ascending); far_off / near_off (nleaves + 1 int64);
  * far_idx (NFAR int32) and near_idx (NNEAR int32), ascending within each leaf.
- * Any pointer may be NULL to skip that array.  Synchronises the device. */
+ * With KDFMM_WALK_DUAL the far lists are per cell: far_off has ncells + 1
+ * entries.  Any pointer may be NULL to skip that array.  Synchronises the
+ * device. */
 int kdfmm_tree_export(kdfmm_tree t, int64_t* perm, int64_t* cell_ints, double* cell_reals,
                       int32_t* leaf_ids, int64_t* far_off, int32_t* far_idx, int64_t* near_off,
                       int32_t* near_idx);

@@ -46,6 +46,9 @@ int check_params(const kdfmm_params* p, const double* h) {
     return set_error(KDFMM_ERR_INVALID_ARG, "r_kern must be finite and >= 0");
   if (p->expansion != KDFMM_EXPANSION_PHANTOM && p->expansion != KDFMM_EXPANSION_STANDARD)
     return set_error(KDFMM_ERR_INVALID_ARG, "unknown expansion %d", p->expansion);
+  if (p->walk != KDFMM_WALK_LEAF && p->walk != KDFMM_WALK_DUAL)
+    return set_error(KDFMM_ERR_INVALID_ARG, "unknown walk %d", p->walk);
+  if (p->reserved != 0) return set_error(KDFMM_ERR_INVALID_ARG, "reserved must be 0");
   if (p->soft_kind == KDFMM_SOFT_M4 && h == nullptr)
     return set_error(KDFMM_ERR_INVALID_ARG, "M4 kernel softening needs smoothing lengths h");
   return KDFMM_OK;
@@ -257,6 +260,7 @@ static kdfmm_tree_s::GraphKey graph_key_of(const kdfmm_tree_s* t, const double* 
   k.far_cap = t->L.far_cap; k.near_cap = t->L.near_cap;
   k.n_sys = t->n_sys; k.cap_sys = t->cap_sys; k.min_nleaf = t->min_nleaf;
   k.soft_kind = t->p.soft_kind; k.precision = t->p.precision; k.r_kern = t->p.r_kern;
+  k.expansion = t->p.expansion; k.walk = t->p.walk;
   return k;
 }
 
@@ -277,6 +281,7 @@ static int enqueue_fixed(kdfmm_tree_s* t, const double* x, const double* m, cons
 static void graph_capture(kdfmm_tree_s* t, const double* x, const double* m, const double* h,
                           double* a, double* phi, cudaStream_t s) {
   graph_drop(t);
+  if (t->p.walk != KDFMM_WALK_LEAF) return;        // the dual walk's queues follow the host
   if (cudaStreamSynchronize(s) != cudaSuccess) {   // the lists may be copied to larger slots
     cudaGetLastError();
     return;
@@ -397,6 +402,7 @@ void kdfmm_tree_destroy(kdfmm_tree t) {
   if (t->host_sys_off) cudaFreeHost(t->host_sys_off);
   graph_drop(t);
   if (t->capture_stream) cudaStreamDestroy(t->capture_stream);
+  free_dual(t);
   for (cudaEvent_t& e : t->ev)
     if (e) cudaEventDestroy(e);
   if (t->host_stats) cudaFreeHost(t->host_stats);
@@ -497,13 +503,14 @@ int kdfmm_fmm_accel(kdfmm_tree t, double* a, double* phi, void* stream) {
     return set_error(KDFMM_ERR_INVALID_ARG, "a (and phi) must be device pointers");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = KDFMM_OK;
+  const bool dual = t->p.walk == KDFMM_WALK_DUAL;
   if (!t->lists_frozen) {              // after kdfmm_tree_moments the lists stay as they were
     phase_begin(t, KDFMM_PHASE_WALK, s);
-    if ((rc = run_walk(t, s))) return rc;
+    if ((rc = dual ? run_dual_walk(t, s) : run_walk(t, s))) return rc;
     phase_end(t, KDFMM_PHASE_WALK, s);
   }
   phase_begin(t, KDFMM_PHASE_M2L, s);
-  if ((rc = run_m2l(t, s))) return rc;
+  if ((rc = dual ? run_dual_local(t, s) : run_m2l(t, s))) return rc;
   phase_end(t, KDFMM_PHASE_M2L, s);
   phase_begin(t, KDFMM_PHASE_P2P, s);
   if ((rc = run_p2p(t, a, phi, s))) return rc;
@@ -596,31 +603,47 @@ int kdfmm_tree_export(kdfmm_tree t, int64_t* perm, int64_t* cell_ints, double* c
   if (leaf_ids && (rc = D2H(leaf_ids, t->leaf_cells, nl * sizeof(int32_t)))) return rc;
   if (far_off || far_idx || near_off || near_idx) {
     if (!t->evaluated) return set_error(KDFMM_ERR_INVALID_ARG, "no evaluation to export lists from");
-    std::vector<int32_t> fc(nl), nc(nl);
-    std::vector<int64_t> fst(nl), nst(nl);
-    if ((rc = D2H(fc.data(), t->L.far_cnt, nl * sizeof(int32_t)))) return rc;
-    if ((rc = D2H(nc.data(), t->L.near_cnt, nl * sizeof(int32_t)))) return rc;
-    if ((rc = D2H(fst.data(), t->L.far_off, nl * sizeof(int64_t)))) return rc;
+    // leaf walk: far and near lists per leaf; dual walk: far lists per cell
+    // (nc rows), near lists per leaf.  Entries ascending in every list.
+    const bool dual = t->p.walk == KDFMM_WALK_DUAL;
+    const int64_t frows = dual ? nc : nl;
+    std::vector<int32_t> fc(frows), nc_(nl);
+    std::vector<int64_t> fst(frows), nst(nl);
+    const int32_t* fcnt = dual ? t->dual.far_cnt : t->L.far_cnt;
+    const int64_t* foff = dual ? t->dual.far_off : t->L.far_off;
+    const int32_t* fidx = dual ? t->dual.far_idx : t->L.far_idx;
+    const int64_t fcap = dual ? t->dual.far_idx_cap : t->L.far_cap;
+    if ((rc = D2H(fc.data(), fcnt, frows * sizeof(int32_t)))) return rc;
+    if ((rc = D2H(nc_.data(), t->L.near_cnt, nl * sizeof(int32_t)))) return rc;
+    if ((rc = D2H(fst.data(), foff, frows * sizeof(int64_t)))) return rc;
     if ((rc = D2H(nst.data(), t->L.near_off, nl * sizeof(int64_t)))) return rc;
     std::vector<int32_t> fs, ns;
     if (far_idx) {
-      fs.resize((size_t)t->L.far_cap);
-      if ((rc = D2H(fs.data(), t->L.far_idx, fs.size() * sizeof(int32_t)))) return rc;
+      fs.resize((size_t)fcap);
+      if (fcap > 0 && (rc = D2H(fs.data(), fidx, fs.size() * sizeof(int32_t)))) return rc;
     }
     if (near_idx) {
       ns.resize((size_t)t->L.near_cap);
       if ((rc = D2H(ns.data(), t->L.near_idx, ns.size() * sizeof(int32_t)))) return rc;
     }
     int64_t fo = 0, no = 0;
-    for (int64_t k = 0; k < nl; ++k) {
+    for (int64_t k = 0; k < frows; ++k) {
       if (far_off) far_off[k] = fo;
-      if (near_off) near_off[k] = no;
-      if (far_idx) memcpy(far_idx + fo, fs.data() + fst[k], fc[k] * sizeof(int32_t));
-      if (near_idx) memcpy(near_idx + no, ns.data() + nst[k], nc[k] * sizeof(int32_t));
+      if (far_idx) {
+        memcpy(far_idx + fo, fs.data() + fst[k], fc[k] * sizeof(int32_t));
+        if (dual) std::sort(far_idx + fo, far_idx + fo + fc[k]);
+      }
       fo += fc[k];
-      no += nc[k];
     }
-    if (far_off) far_off[nl] = fo;
+    for (int64_t k = 0; k < nl; ++k) {
+      if (near_off) near_off[k] = no;
+      if (near_idx) {
+        memcpy(near_idx + no, ns.data() + nst[k], nc_[k] * sizeof(int32_t));
+        if (dual) std::sort(near_idx + no, near_idx + no + nc_[k]);
+      }
+      no += nc_[k];
+    }
+    if (far_off) far_off[frows] = fo;
     if (near_off) near_off[nl] = no;
   }
   return KDFMM_OK;
@@ -629,6 +652,8 @@ int kdfmm_tree_export(kdfmm_tree t, int64_t* perm, int64_t* cell_ints, double* c
 int kdfmm_fmm_accel_vjp(kdfmm_tree t, const double* a_bar, double* x_bar, double* m_bar,
                         void* stream) {
   if (!t || !t->evaluated) return set_error(KDFMM_ERR_INVALID_ARG, "no evaluation to differentiate");
+  if (t->p.walk != KDFMM_WALK_LEAF)
+    return set_error(KDFMM_ERR_INVALID_ARG, "the adjoint covers the leaf-only walk only");
   if (!is_device_ptr(a_bar) || !is_device_ptr(x_bar) || !is_device_ptr(m_bar))
     return set_error(KDFMM_ERR_INVALID_ARG, "a_bar, x_bar and m_bar must be device pointers");
   return run_vjp(t, a_bar, x_bar, m_bar, static_cast<cudaStream_t>(stream));

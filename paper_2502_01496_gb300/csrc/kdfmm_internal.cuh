@@ -168,16 +168,34 @@ struct kdfmm_tree_s {
   int32_t* host_counters = nullptr;
   int64_t launches = 0;            // kernels launched by this handle
 
+  // symmetric dual-tree walk (KDFMM_WALK_DUAL): pair queues, the far and near
+  // pair lists, per-cell far lists and per-cell local expansions
+  struct Dual {
+    int2 *q[2] = {nullptr, nullptr}, *far = nullptr, *near = nullptr;
+    int64_t q_cap = 0, far_cap = 0, near_cap = 0;
+    int32_t* ctr = nullptr;              // device: [0] queue out, [1] far pairs, [2] near pairs, [3] overflow
+    int64_t* np2p = nullptr;             // device: particle pairs of the near list
+    int32_t* far_cnt = nullptr;          // per cell
+    int64_t* far_off = nullptr;          // per cell + 1
+    int32_t* far_idx = nullptr;
+    int64_t far_idx_cap = 0, cells_cap = 0;
+    int32_t* cursor = nullptr;           // per cell (fill cursors)
+    float* lcell32 = nullptr;            // 24 per cell
+    double* lcell64 = nullptr;           // 20 per cell
+    int64_t nfar = 0, nnear = 0;         // entries (both directions)
+  } dual;
+
   // captured evaluation (kdfmm_fmm_accel_batched): valid for the arguments
   // and buffers it was captured with
   struct GraphKey {
     const void *x, *m, *h;
     void *a, *phi;
     int64_t n, cap_n, cap_far, cap_near, far_cap, near_cap;
-    int32_t n_sys, cap_sys, min_nleaf, soft_kind, precision;
+    int32_t n_sys, cap_sys, min_nleaf, soft_kind, precision, expansion, walk;
     double r_kern;
     bool operator==(const GraphKey& o) const {
       return x == o.x && m == o.m && h == o.h && a == o.a && phi == o.phi && n == o.n &&
+             expansion == o.expansion && walk == o.walk &&
              cap_n == o.cap_n && cap_far == o.cap_far && cap_near == o.cap_near &&
              far_cap == o.far_cap && near_cap == o.near_cap && n_sys == o.n_sys &&
              cap_sys == o.cap_sys && min_nleaf == o.min_nleaf && soft_kind == o.soft_kind &&
@@ -384,6 +402,13 @@ int run_walk(kdfmm_tree_s* t, cudaStream_t s);
 int ensure_slots(kdfmm_tree_s* t, int slot_leaves);
 int walk_fixed(kdfmm_tree_s* t, int slot_leaves, cudaStream_t s);
 int run_m2l(kdfmm_tree_s* t, cudaStream_t s);
+int run_m2l_cells(kdfmm_tree_s* t, const int32_t* far_cnt, const int64_t* far_off,
+                  const int32_t* far_idx, float* out32, double* out64, cudaStream_t s);
+// symmetric dual-tree walk: lists (per-cell far, per-leaf near), then the
+// per-cell M2L and the translation of every cell's expansion to its leaves
+int run_dual_walk(kdfmm_tree_s* t, cudaStream_t s);
+int run_dual_local(kdfmm_tree_s* t, cudaStream_t s);
+void free_dual(kdfmm_tree_s* t);
 int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s);
 int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, cudaStream_t s);
 int momentum(const double* m, const double* v, int64_t n, double* out, double* scratch,

@@ -115,6 +115,7 @@ struct M2LArgs {
   const int32_t* counters;   // counters[C_LEAVES]: leaves
   int64_t cap_far;           // entries a list may hold (slot size, or no limit)
   int max_leaves;            // leaves the lists were made for
+  int nsinks;                // > 0: sinks are cells 0 .. nsinks-1 (leaf_cells unused)
   const int32_t* far_cnt;
   const int32_t* far_idx;
   const int64_t* far_off;
@@ -127,10 +128,10 @@ struct M2LArgs {
 template <bool STD>
 __global__ void __launch_bounds__(256) k_m2l_mixed(M2LArgs A) {
   const int lane = threadIdx.x & 31;
-  const int nleaves = min(A.counters[C_LEAVES], A.max_leaves);
+  const int nleaves = A.nsinks > 0 ? A.nsinks : min(A.counters[C_LEAVES], A.max_leaves);
   for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < nleaves;
        k += (int)((gridDim.x * blockDim.x) >> 5)) {
-  const int a = A.leaf_cells[k];
+  const int a = A.nsinks > 0 ? k : A.leaf_cells[k];
   const float4 ah = A.src32[4 * a], al = A.src32[4 * a + 1];
   float acc[20], lo[4];
 #pragma unroll
@@ -182,10 +183,10 @@ __global__ void __launch_bounds__(256) k_m2l_mixed(M2LArgs A) {
 template <bool STD>
 __global__ void __launch_bounds__(256) k_m2l_fp64(M2LArgs A) {
   const int lane = threadIdx.x & 31;
-  const int nleaves = min(A.counters[C_LEAVES], A.max_leaves);
+  const int nleaves = A.nsinks > 0 ? A.nsinks : min(A.counters[C_LEAVES], A.max_leaves);
   for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < nleaves;
        k += (int)((gridDim.x * blockDim.x) >> 5)) {
-  const int a = A.leaf_cells[k];
+  const int a = A.nsinks > 0 ? k : A.leaf_cells[k];
   const double* sa = A.src64 + 10 * (int64_t)a;
   const double ax = sa[0], ay = sa[1], az = sa[2];
   double acc[20];
@@ -243,6 +244,37 @@ int run_m2l(kdfmm_tree_s* t, cudaStream_t s) {
   }
   t->launches += 1;
   return check_cuda(cudaGetLastError(), "m2l launch");
+}
+
+// M2L into every cell from per-cell far lists (the dual walk): sink cell c's
+// list is far_idx[far_off[c] ...) with far_cnt[c] entries; the coefficients go
+// to out32 (24 floats per cell) or out64 (20 doubles per cell).
+int run_m2l_cells(kdfmm_tree_s* t, const int32_t* far_cnt, const int64_t* far_off,
+                  const int32_t* far_idx, float* out32, double* out64, cudaStream_t s) {
+  M2LArgs A{};
+  A.leaf_cells = nullptr;
+  A.counters = t->counters;
+  A.cap_far = INT64_MAX;
+  A.max_leaves = t->ncells;
+  A.nsinks = t->ncells;
+  A.far_cnt = far_cnt;
+  A.far_off = far_off;
+  A.far_idx = far_idx;
+  A.src32 = t->c.src32;
+  A.src64 = t->c.src64;
+  A.lexp32 = out32;
+  A.lexp64 = out64;
+  const unsigned g = blocks_for((int64_t)std::max(t->ncells, 1) * 32, 256);
+  const bool std_exp = t->p.expansion == KDFMM_EXPANSION_STANDARD;
+  if (t->p.precision == KDFMM_MIXED) {
+    if (std_exp) k_m2l_mixed<true><<<g, 256, 0, s>>>(A);
+    else k_m2l_mixed<false><<<g, 256, 0, s>>>(A);
+  } else {
+    if (std_exp) k_m2l_fp64<true><<<g, 256, 0, s>>>(A);
+    else k_m2l_fp64<false><<<g, 256, 0, s>>>(A);
+  }
+  t->launches += 1;
+  return check_cuda(cudaGetLastError(), "m2l (cells) launch");
 }
 
 }  // namespace kdfmm

@@ -28,6 +28,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "CAPACITY
 SOFT_PLUMMER, SOFT_M4 = 0, 1
 FP64, MIXED = 0, 1
 EXPANSION_PHANTOM, EXPANSION_STANDARD = 0, 1
+WALK_LEAF, WALK_DUAL = 0, 1
 MAX_LEAF = 32
 STAT_NAMES = ("n", "ncells", "nleaves", "depth", "nfar", "nnear", "np2p", "nfallback", "nexact",
               "launches")
@@ -43,15 +44,17 @@ class KdfmmError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("eps", ctypes.c_double), ("r_kern", ctypes.c_double),
                 ("n_leaf", ctypes.c_int32), ("soft_kind", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("expansion", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("expansion", ctypes.c_int32),
+                ("walk", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def make_params(theta=0.5, eps=0.01, r_kern=2.0, n_leaf=16, soft_kind=SOFT_PLUMMER,
-                precision=MIXED, expansion=0) -> Params:
+                precision=MIXED, expansion=0, walk=0) -> Params:
     """expansion: 0 = Eq. 6 at full order (the paper's scheme), 1 = the standard
-    p = 3 Cartesian series."""
+    p = 3 Cartesian series.  walk: 0 = the paper's leaf-only walk, 1 = the
+    symmetric dual-tree walk."""
     return Params(float(theta), float(eps), float(r_kern), int(n_leaf), int(soft_kind),
-                  int(precision), int(expansion))
+                  int(precision), int(expansion), int(walk), 0)
 
 
 _lib = None
@@ -299,7 +302,9 @@ class Export:
     near_idx: np.ndarray | None
 
 
-def tree_export(tree, lists: bool = True) -> Export:
+def tree_export(tree, lists: bool = True, dual: bool = False) -> Export:
+    """Host copies of the tree and lists; with dual=True (the dual walk) the far
+    lists are per cell (far_off has ncells + 1 entries)."""
     st = tree_stats(tree)
     n, nc, nl = st["n"], st["ncells"], st["nleaves"]
     perm = np.empty(n, dtype=np.int64)
@@ -308,7 +313,7 @@ def tree_export(tree, lists: bool = True) -> Export:
     leaf = np.empty(nl, dtype=np.int32)
     fo = fi = no = ni = None
     if lists:
-        fo = np.empty(nl + 1, dtype=np.int64)
+        fo = np.empty((nc if dual else nl) + 1, dtype=np.int64)
         no = np.empty(nl + 1, dtype=np.int64)
         fi = np.empty(max(st["nfar"], 1), dtype=np.int32)
         ni = np.empty(max(st["nnear"], 1), dtype=np.int32)
@@ -380,4 +385,4 @@ class KdFmm:
         return tree_stats(self.handle)
 
     def export(self, lists: bool = True) -> Export:
-        return tree_export(self.handle, lists)
+        return tree_export(self.handle, lists, dual=self.params.walk == WALK_DUAL)

@@ -48,8 +48,9 @@ def test_binding_rejects_null_handles_without_a_gpu(libpath):
 
 def test_params_struct_layout_matches_header():
     from paper_2502_01496_gb300 import native
-    assert ctypes.sizeof(native.Params) == 40
+    assert ctypes.sizeof(native.Params) == 48
     assert native.Params.n_leaf.offset == 24 and native.Params.expansion.offset == 36
+    assert native.Params.walk.offset == 40 and native.Params.reserved.offset == 44
 
 
 def test_forest_arguments_are_checked_on_the_host(libpath):
