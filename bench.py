@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--batched-steps", type=int, default=5,
                     help="steps of the 256-system batch (0 skips it)")
+    ap.add_argument("--variant-steps", type=int, default=5,
+                    help="steps of the dual-walk and standard-expansion variants (0 skips them)")
     return ap.parse_args()
 
 
@@ -311,6 +313,48 @@ def run_batched(args, dev, flush):
     return out
 
 
+def run_variants(args, ps, x, m, h, flush):
+    """The same workload under the method's variants: the paper's leaf-only walk
+    with Eq. 6 (the headline), the symmetric dual-tree walk, and the standard
+    p = 3 expansion -- time per evaluation and the relative total force
+    |sum m a| / sum m |a| that the leaf-only walk leaves (Sec. 4)."""
+    import torch
+    from paper_2502_01496_gb300 import native
+    out = {}
+    n = ps.n
+    a = torch.empty((n, 3), dtype=torch.float64, device=x.device)
+    F = torch.empty(3, dtype=torch.float64, device=x.device)
+    prec = native.MIXED if args.precision == "mixed" else native.FP64
+    for label, walk, expansion in (("leaf_walk", 0, 0), ("dual_walk", 1, 0),
+                                   ("standard_expansion", 0, 1)):
+        f = native.KdFmm(theta=args.theta, eps=ps.eps, r_kern=2.0, n_leaf=args.n_leaf,
+                         soft_kind=ps.soft_kind, precision=prec, walk=walk, expansion=expansion)
+        for _ in range(2):
+            f.build(x, m, h)
+            f.accel(a, None, want_phi=False)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.variant_steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f.build(x, m, h)
+            f.accel(a, None, want_phi=False)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        native.total_momentum(m, a, F)
+        rel = float(torch.linalg.norm(F) / (m * torch.linalg.norm(a, dim=1)).sum())
+        st = f.stats()
+        ms = statistics.mean(ts)
+        out[label] = {"value": n / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_eval": ms,
+                      "rel_total_force": rel, "p2p": st["np2p"], "m2l": st["nfar"],
+                      "near": st["nnear"]}
+        del f
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -464,6 +508,9 @@ def run_ours(args):
     batched = None
     if args.batched_steps > 0:
         batched = run_batched(args, dev, flush)
+    variants = None
+    if args.variant_steps > 0:
+        variants = run_variants(args, ps, x, m, h, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -482,6 +529,7 @@ def run_ours(args):
             "mixed_over_fp64": (value / world / fp64["value"]) if fp64 else None,
             "phases_ms": phase_mean,
             "batched": batched,
+            "variants": variants,
             "interactions": {"p2p": st["np2p"], "m2l": st["nfar"], "nleaves": st["nleaves"],
                              "ncells": st["ncells"], "p2p_per_s": st["np2p"] / (ms_per_step / 1e3),
                              "m2l_per_s": st["nfar"] / (ms_per_step / 1e3)},
