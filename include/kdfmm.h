@@ -188,8 +188,9 @@ int kdfmm_fmm_accel(kdfmm_tree t, double* a, double* phi, void* stream);
  * dual numbers, M and Q linear), P2P on the target and on the source side,
  * and the moments (com = sum m x / M, Q of Eq. 7) back to the particles.
  * a_bar: N x 3 cotangent (caller order, device); x_bar: N x 3 and m_bar: N
- * outputs (device, overwritten).  Arithmetic is float64 in both precision
- * modes (mixed mode uses the evaluation's float32 expansions); cell
+ * outputs (device, overwritten).  FP64 mode runs every step in float64;
+ * mixed mode forms the M2L r-derivatives and the P2P pair terms in float32
+ * (as its evaluation does) from float64 differences, with float64 sums.  Cell
  * cotangents and the P2P source-side terms are summed with float64 atomics,
  * so the last bits may vary run to run.  Allocates its scratch (88 bytes per
  * particle, 160 per leaf, 80 per cell) with cudaMallocAsync on `stream`.  Errors:

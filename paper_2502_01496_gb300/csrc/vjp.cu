@@ -1,7 +1,9 @@
 // Vector-Jacobian product of one force evaluation with respect to positions
 // and masses, through the same tree and interaction lists (topology, lists
 // and smoothing lengths held fixed).  The paper has no adjoint; this is the
-// derivative of the evaluation of Sec. 2 (Eqs. 3, 6, 7, 8, 13), in float64.
+// derivative of the evaluation of Sec. 2 (Eqs. 3, 6, 7, 8, 13).  FP64 mode
+// runs every step in float64; mixed mode runs the M2L and P2P reverses with
+// float32 terms (as its forward does) and float64 sums.
 //
 // a_i = sum_{j in near(leaf i), j != i} m_j K(x_i - x_j)            (P2P)
 //     + L(C_alpha, x_i - com_alpha)                                (L2P, Eq. 8)
@@ -28,28 +30,41 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 // ---------------------------------------------------------------------------
 // M2L coefficients (same closed forms as the forward) on a dual-number type
 // ---------------------------------------------------------------------------
-struct Dual3 {
-  double v, d[3];
+// S: the scalar (double, or float in mixed mode); d holds the derivatives
+// with respect to the three components of r.
+template <class S>
+struct DualT {
+  S v, d[3];
 };
-__device__ __forceinline__ Dual3 dconst(double v) { return Dual3{v, {0.0, 0.0, 0.0}}; }
-__device__ __forceinline__ Dual3 operator+(const Dual3& a, const Dual3& b) {
-  return Dual3{a.v + b.v, {a.d[0] + b.d[0], a.d[1] + b.d[1], a.d[2] + b.d[2]}};
+template <class S>
+__device__ __forceinline__ DualT<S> operator+(const DualT<S>& a, const DualT<S>& b) {
+  return DualT<S>{a.v + b.v, {a.d[0] + b.d[0], a.d[1] + b.d[1], a.d[2] + b.d[2]}};
 }
-__device__ __forceinline__ Dual3 operator-(const Dual3& a, const Dual3& b) {
-  return Dual3{a.v - b.v, {a.d[0] - b.d[0], a.d[1] - b.d[1], a.d[2] - b.d[2]}};
+template <class S>
+__device__ __forceinline__ DualT<S> operator-(const DualT<S>& a, const DualT<S>& b) {
+  return DualT<S>{a.v - b.v, {a.d[0] - b.d[0], a.d[1] - b.d[1], a.d[2] - b.d[2]}};
 }
-__device__ __forceinline__ Dual3 operator-(const Dual3& a) {
-  return Dual3{-a.v, {-a.d[0], -a.d[1], -a.d[2]}};
+template <class S>
+__device__ __forceinline__ DualT<S> operator-(const DualT<S>& a) {
+  return DualT<S>{-a.v, {-a.d[0], -a.d[1], -a.d[2]}};
 }
-__device__ __forceinline__ Dual3 operator*(const Dual3& a, const Dual3& b) {
-  return Dual3{a.v * b.v,
-               {a.d[0] * b.v + a.v * b.d[0], a.d[1] * b.v + a.v * b.d[1], a.d[2] * b.v + a.v * b.d[2]}};
+template <class S>
+__device__ __forceinline__ DualT<S> operator*(const DualT<S>& a, const DualT<S>& b) {
+  return DualT<S>{a.v * b.v,
+                  {a.d[0] * b.v + a.v * b.d[0], a.d[1] * b.v + a.v * b.d[1],
+                   a.d[2] * b.v + a.v * b.d[2]}};
 }
-__device__ __forceinline__ Dual3& operator+=(Dual3& a, const Dual3& b) { return a = a + b; }
-__device__ __forceinline__ Dual3 rsqrt_dual(const Dual3& a) {
-  const double r = 1.0 / sqrt(a.v);
-  const double dr = -0.5 * r / a.v;
-  return Dual3{r, {dr * a.d[0], dr * a.d[1], dr * a.d[2]}};
+template <class S>
+__device__ __forceinline__ DualT<S>& operator+=(DualT<S>& a, const DualT<S>& b) { return a = a + b; }
+
+__device__ __forceinline__ double rsq(double v) { return 1.0 / sqrt(v); }
+__device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
+
+template <class S>
+__device__ __forceinline__ DualT<S> rsqrt_dual(const DualT<S>& a) {
+  const S r = rsq(a.v);
+  const S dr = S(-0.5) * r / a.v;
+  return DualT<S>{r, {dr * a.d[0], dr * a.d[1], dr * a.d[2]}};
 }
 
 template <class T>
@@ -57,10 +72,20 @@ __device__ __forceinline__ T tc(double v);
 template <>
 __device__ __forceinline__ double tc<double>(double v) { return v; }
 template <>
-__device__ __forceinline__ Dual3 tc<Dual3>(double v) { return dconst(v); }
+__device__ __forceinline__ float tc<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ DualT<double> tc<DualT<double>>(double v) {
+  return DualT<double>{v, {0.0, 0.0, 0.0}};
+}
+template <>
+__device__ __forceinline__ DualT<float> tc<DualT<float>>(double v) {
+  return DualT<float>{(float)v, {0.0f, 0.0f, 0.0f}};
+}
 
-__device__ __forceinline__ double rs(double v) { return 1.0 / sqrt(v); }
-__device__ __forceinline__ Dual3 rs(const Dual3& v) { return rsqrt_dual(v); }
+__device__ __forceinline__ double rs(double v) { return rsq(v); }
+__device__ __forceinline__ float rs(float v) { return rsq(v); }
+template <class S>
+__device__ __forceinline__ DualT<S> rs(const DualT<S>& v) { return rsqrt_dual(v); }
 
 template <class T>
 __device__ __forceinline__ T c2e(int a, int b, const T R[3], const T u[3], const T Qm[3][3], T s1,
@@ -252,8 +277,10 @@ __global__ void k_vjp_l2p(VjpArgs V) {
   }
 }
 
-// M2L reverse: warp per sink leaf, lanes over its far cells.
-template <bool STD>
+// M2L reverse: warp per sink leaf, lanes over its far cells.  S: arithmetic
+// of the coefficients (float in mixed mode, as in the forward); r is formed
+// in float64 and every sum is kept in float64.
+template <bool STD, class S>
 __global__ void k_vjp_m2l(VjpArgs V) {
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -268,19 +295,19 @@ __global__ void k_vjp_m2l(VjpArgs V) {
   const double zq[6] = {0, 0, 0, 0, 0, 0};
   for (int e = lane; e < nf; e += 32) {
     const int b = V.far_idx[off + e];
-    const double r[3] = {ax - V.c.cx[b], ay - V.c.cy[b], az - V.c.cz[b]};
+    const S r[3] = {(S)(ax - V.c.cx[b]), (S)(ay - V.c.cy[b]), (S)(az - V.c.cz[b])};
     const double* Qb = V.c.Q + 6 * (int64_t)b;
     // r-derivatives of sum_j cb_j C_j by dual numbers; M and Q enter linearly
-    const Dual3 R[3] = {Dual3{r[0], {1.0, 0.0, 0.0}}, Dual3{r[1], {0.0, 1.0, 0.0}},
-                        Dual3{r[2], {0.0, 0.0, 1.0}}};
-    const Dual3 cr = m2l_contract<Dual3, STD>(R, V.c.M[b], Qb, cb);
-    const double gr[3] = {cr.d[0], cr.d[1], cr.d[2]};
-    const double mbar = m2l_contract<double, STD>(r, 1.0, zq, cb);
+    const DualT<S> R[3] = {DualT<S>{r[0], {S(1), S(0), S(0)}}, DualT<S>{r[1], {S(0), S(1), S(0)}},
+                           DualT<S>{r[2], {S(0), S(0), S(1)}}};
+    const DualT<S> cr = m2l_contract<DualT<S>, STD>(R, V.c.M[b], Qb, cb);
+    const double gr[3] = {(double)cr.d[0], (double)cr.d[1], (double)cr.d[2]};
+    const double mbar = (double)m2l_contract<S, STD>(r, 1.0, zq, cb);
     double qbar[6];
     for (int qq = 0; qq < 6; ++qq) {
       double eq[6] = {0, 0, 0, 0, 0, 0};
       eq[qq] = 1.0;
-      qbar[qq] = m2l_contract<double, STD>(r, 0.0, eq, cb);
+      qbar[qq] = (double)m2l_contract<S, STD>(r, 0.0, eq, cb);
     }
     rx += gr[0]; ry += gr[1]; rz += gr[2];
     double* cbb = V.cell_bar + 10 * (int64_t)b;
@@ -305,50 +332,59 @@ __global__ void k_vjp_m2l(VjpArgs V) {
 }
 
 // Pair kernel K (a_i += m_j K(d), d = x_i - x_j) and (J b) for J = dK/dd.
-__device__ __forceinline__ double m4_F(double q) {
-  if (q < 1.0) return q * q * q * (4.0 / 3.0 - 1.2 * q * q + 0.5 * q * q * q);
-  if (q < 2.0) { const double t = 2.0 - q; return 1.0 - t * t * t * t * (1.0 - 0.8 * t + t * t / 6.0); }
-  return 1.0;
+// M4 mass fraction F(q) for 1 <= q < 2, and 4 pi w(q) (the M4 kernel times 4 pi).
+template <class S>
+__device__ __forceinline__ S m4_F_outer(S q) {
+  const S t = S(2) - q;
+  return S(1) - t * t * t * t * (S(1) - S(0.8) * t + t * t / S(6));
 }
-__device__ __forceinline__ double m4_w4pi(double q) {      // 4 pi w(q)
-  if (q < 1.0) return 4.0 * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
-  if (q < 2.0) { const double t = 2.0 - q; return t * t * t; }
-  return 0.0;
+template <class S>
+__device__ __forceinline__ S m4_w4pi(S q) {
+  if (q < S(1)) return S(4) * (S(1) - S(1.5) * q * q + S(0.75) * q * q * q);
+  if (q < S(2)) { const S t = S(2) - q; return t * t * t; }
+  return S(0);
 }
 // K(d) = -f(r) d with J = dK/dd = -f I - g d d^T, g = f'(r) / r.  Plummer:
-// f = (r^2 + eps^2)^(-3/2).  M4 (Eq. 13, symmetrised): the mean of the two
-// sides' F(q) / (q^3 h^3) inside the support (1/r^3 outside), whose r-derivative
-// over r is (F'(q) q - 3 F(q)) / (q^5 h^5) with F' = 4 pi w q^2; at r = 0 the
-// side's f is 4 / (3 h^3) and its g is finite and multiplies d = 0.
-__device__ __forceinline__ void pair_fg(int kind, double r2, double eps2, double hi, double hj,
-                                        double& f, double& g) {
+// f = (r^2 + eps^2)^(-3/2), g = -3 (r^2 + eps^2)^(-5/2).  M4 (Eq. 13,
+// symmetrised): the mean of the two sides' terms; one side, q = r/h:
+//   q < 1:       f = (4/3 - 6/5 q^2 + q^3/2) / h^3,   g = (-12/5 + 3/2 q) / h^5
+//   1 <= q < 2:  f = F(q) / (q^3 h^3),  g = (F'(q) q - 3 F(q)) / (q^5 h^5), F' = 4 pi w q^2
+//   q >= 2:      f = 1 / r^3,           g = -3 / r^5
+// (the q < 1 forms are the polynomials themselves, finite at r = 0, where g
+// multiplies d = 0).
+template <class S>
+__device__ __forceinline__ void pair_fg(int kind, S r2, S eps2, S hi, S hj, S& f, S& g) {
   if (kind == KDFMM_SOFT_PLUMMER) {
-    const double s2 = r2 + eps2;
-    const double inv = 1.0 / sqrt(s2);
-    const double inv3 = inv * inv * inv;
+    const S inv = rsq(r2 + eps2);
+    const S inv3 = inv * inv * inv;
     f = inv3;
-    g = -3.0 * inv3 * inv * inv;
+    g = S(-3) * inv3 * inv * inv;
     return;
   }
-  const double r = sqrt(r2);
-  double fs = 0.0, gs = 0.0;
-  const double hs[2] = {hi, hj};
+  const S r = sqrt(r2);
+  S fs = S(0), gs = S(0);
+  const S hs[2] = {hi, hj};
   for (int side = 0; side < 2; ++side) {
-    const double h = hs[side];
-    const double q = r / h;
-    if (q >= 2.0) {
-      fs += 1.0 / (r2 * r);
-      gs += -3.0 / (r2 * r2 * r);
-    } else if (r2 == 0.0) {
-      fs += 4.0 / (3.0 * h * h * h);
+    const S h = hs[side];
+    const S hinv = S(1) / h;
+    const S q = r * hinv;
+    const S h3inv = hinv * hinv * hinv;
+    if (q >= S(2)) {
+      const S rinv = S(1) / r;
+      const S r3inv = rinv * rinv * rinv;
+      fs += r3inv;
+      gs += S(-3) * r3inv * rinv * rinv;
+    } else if (q < S(1)) {
+      fs += (S(4) / S(3) + q * q * (S(-1.2) + S(0.5) * q)) * h3inv;
+      gs += (S(-2.4) + S(1.5) * q) * h3inv * hinv * hinv;
     } else {
-      const double h3 = h * h * h, q2 = q * q;
-      fs += m4_F(q) / (q2 * q * h3);
-      gs += (m4_w4pi(q) * q2 * q - 3.0 * m4_F(q)) / (q2 * q2 * q * h3 * h * h);
+      const S q2 = q * q, F = m4_F_outer(q);
+      fs += F / (q2 * q) * h3inv;
+      gs += (m4_w4pi(q) * q2 * q - S(3) * F) / (q2 * q2 * q) * h3inv * hinv * hinv;
     }
   }
-  f = 0.5 * fs;
-  g = 0.5 * gs;
+  f = S(0.5) * fs;
+  g = S(0.5) * gs;
 }
 
 // P2P reverse, warp per target leaf, lanes = (target, slice) as in the
@@ -356,6 +392,9 @@ __device__ __forceinline__ void pair_fg(int kind, double r2, double eps2, double
 // lane; the source side (x_bar_j -= m_j J(d) a_bar_i, m_bar_j += K(d).a_bar_i)
 // is summed over the leaf's targets by shuffles and added with one float64
 // atomic per source into separate arrays.
+// S: arithmetic of the pair terms (float in mixed mode); differences of
+// positions are formed in float64 first and every sum is kept in float64.
+template <class S>
 __global__ void k_vjp_p2p(VjpArgs V) {
   const unsigned full = 0xffffffffu;
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -367,7 +406,7 @@ __global__ void k_vjp_p2p(VjpArgs V) {
   const bool act = sl < K;
   const int64_t pi = (int64_t)fa + t;
   const double xi = V.tp.x[pi], yi = V.tp.y[pi], zi = V.tp.z[pi], hi = V.tp.h[pi];
-  const double b[3] = {V.ab[3 * pi], V.ab[3 * pi + 1], V.ab[3 * pi + 2]};
+  const S bS[3] = {(S)V.ab[3 * pi], (S)V.ab[3 * pi + 1], (S)V.ab[3 * pi + 2]};
   const double eps = V.sys_eps[V.leaf_sys[k]], eps2 = eps * eps;
   double gx = 0.0, gy = 0.0, gz = 0.0;
   const int64_t e0 = V.near_off[k];
@@ -379,32 +418,32 @@ __global__ void k_vjp_p2p(VjpArgs V) {
     for (int it = 0; it < iters; ++it) {
       const int j = sl + K * it;
       const int64_t pj = (int64_t)fb + j;
-      double sx = 0.0, sy = 0.0, sz = 0.0, sm = 0.0;
+      S sx = S(0), sy = S(0), sz = S(0), sm = S(0);
       if (act && j < nb && pj != pi) {
-        const double d[3] = {xi - V.tp.x[pj], yi - V.tp.y[pj], zi - V.tp.z[pj]};
-        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        double f, g;
-        pair_fg(V.soft_kind, r2, eps2, hi, V.tp.h[pj], f, g);
-        const double db = d[0] * b[0] + d[1] * b[1] + d[2] * b[2];
-        const double mj = V.tp.m[pj];
+        const S d[3] = {(S)(xi - V.tp.x[pj]), (S)(yi - V.tp.y[pj]), (S)(zi - V.tp.z[pj])};
+        const S r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        S f, g;
+        pair_fg<S>(V.soft_kind, r2, (S)eps2, (S)hi, (S)V.tp.h[pj], f, g);
+        const S db = d[0] * bS[0] + d[1] * bS[1] + d[2] * bS[2];
+        const S mj = (S)V.tp.m[pj];
         // J b = -f b - (f'/r) d (d.b)
-        const double jx = -f * b[0] - g * d[0] * db;
-        const double jy = -f * b[1] - g * d[1] * db;
-        const double jz = -f * b[2] - g * d[2] * db;
-        gx += mj * jx; gy += mj * jy; gz += mj * jz;
+        const S jx = -f * bS[0] - g * d[0] * db;
+        const S jy = -f * bS[1] - g * d[1] * db;
+        const S jz = -f * bS[2] - g * d[2] * db;
+        gx += (double)(mj * jx); gy += (double)(mj * jy); gz += (double)(mj * jz);
         sx = -mj * jx; sy = -mj * jy; sz = -mj * jz;
         sm = -f * db;                                          // K(d) . a_bar_i
       }
       for (int o = 1; o < nt; o <<= 1) {                       // over the slice's targets
-        const double ox = __shfl_down_sync(full, sx, o), oy = __shfl_down_sync(full, sy, o);
-        const double oz = __shfl_down_sync(full, sz, o), om = __shfl_down_sync(full, sm, o);
+        const S ox = __shfl_down_sync(full, sx, o), oy = __shfl_down_sync(full, sy, o);
+        const S oz = __shfl_down_sync(full, sz, o), om = __shfl_down_sync(full, sm, o);
         if (t + o < nt) { sx += ox; sy += oy; sz += oz; sm += om; }
       }
       if (t == 0 && act && j < nb) {
-        atomicAdd(&V.xsrc[3 * pj], sx);
-        atomicAdd(&V.xsrc[3 * pj + 1], sy);
-        atomicAdd(&V.xsrc[3 * pj + 2], sz);
-        atomicAdd(&V.msrc[pj], sm);
+        atomicAdd(&V.xsrc[3 * pj], (double)sx);
+        atomicAdd(&V.xsrc[3 * pj + 1], (double)sy);
+        atomicAdd(&V.xsrc[3 * pj + 2], (double)sz);
+        atomicAdd(&V.msrc[pj], (double)sm);
       }
     }
   }
@@ -517,11 +556,17 @@ int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, 
   cudaMemsetAsync(V.cell_bar, 0, (size_t)nc * 10 * sizeof(double), s);
   k_gather_abar<<<blocks_for(n, 256), 256, 0, s>>>(a_bar, V);
   k_vjp_l2p<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
-  if (t->p.expansion == KDFMM_EXPANSION_STANDARD)
-    k_vjp_m2l<true><<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
-  else
-    k_vjp_m2l<false><<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
-  k_vjp_p2p<<<blocks_for((int64_t)nl * 32, 128), 128, 0, s>>>(V);
+  const unsigned gw = blocks_for((int64_t)nl * 32, 128);
+  const bool std_exp = t->p.expansion == KDFMM_EXPANSION_STANDARD;
+  if (V.mixed) {
+    if (std_exp) k_vjp_m2l<true, float><<<gw, 128, 0, s>>>(V);
+    else k_vjp_m2l<false, float><<<gw, 128, 0, s>>>(V);
+    k_vjp_p2p<float><<<gw, 128, 0, s>>>(V);
+  } else {
+    if (std_exp) k_vjp_m2l<true, double><<<gw, 128, 0, s>>>(V);
+    else k_vjp_m2l<false, double><<<gw, 128, 0, s>>>(V);
+    k_vjp_p2p<double><<<gw, 128, 0, s>>>(V);
+  }
   k_vjp_moments<<<blocks_for(nl, 128), 128, 0, s>>>(V);
   k_scatter_bar<<<blocks_for(n, 256), 256, 0, s>>>(V, x_bar, m_bar);
   t->launches += 6;

@@ -14,6 +14,10 @@ study measures that drift with the GPU path:
 * `--study force`: the relative total force |sum m a| / sum m |a| of one
   evaluation against N and theta (polytrope binaries), with the fit
   |sum m a| / sum m |a| ~ c N^(-q).
+* `--study gradient`: the drift's sensitivity -- the gradient of
+  L = w . (com(T) - com(0)) with respect to the initial positions of a Plummer
+  sphere in equilibrium, through a checkpointed leapfrog (the adjoint of
+  every force evaluation, trees rebuilt as in the forward run).
 
 Writes one JSON document (stdout, or --out).  Run on the GPU:
   python -m paper_2502_01496_gb300.drift --study binary --n-per-star 1048576
@@ -101,9 +105,42 @@ def study_force(n_list, thetas, precision: int):
     return {"rows": rows, "fits": fits}
 
 
+def study_gradient(n: int, steps: int, dt: float, every: int, theta: float, precision: int):
+    import torch
+    from . import dynamics
+    from . import workloads as W
+    ps = W.plummer(n, W.seed_for(4))
+    v0 = W.plummer_velocities(ps.x, W.seed_for(4, 3))
+    params = dict(theta=theta, eps=ps.eps, n_leaf=16, soft_kind=0, precision=precision)
+    m = torch.tensor(ps.m, device="cuda")
+    w = torch.tensor([0.6, 0.0, 0.8], dtype=torch.float64, device="cuda")
+    x0 = torch.tensor(ps.x, device="cuda").requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xT, _, _ = dynamics.leapfrog(x0, torch.tensor(v0, device="cuda"), m, steps=steps, dt=dt,
+                                 checkpoint_every=every, **params)
+    loss = (w * (dynamics.centre_of_mass(xT, m) - dynamics.centre_of_mass(x0, m))).sum()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    g = x0.grad
+    # the displacement of the centre of mass does not change when every particle
+    # is moved by the same vector: the gradient sums to zero (up to rounding)
+    return {"n": n, "steps": steps, "dt": dt, "checkpoint_every": every, "theta": theta,
+            "precision": "mixed" if precision == 1 else "fp64",
+            "loss": float(loss.detach()), "grad_norm": float(g.norm()),
+            "grad_max": float(g.abs().max()), "grad_sum": g.sum(0).tolist(),
+            "forward_s": t1 - t0, "backward_s": t2 - t1}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--study", choices=["binary", "force"], default="binary")
+    ap.add_argument("--study", choices=["binary", "force", "gradient"], default="binary")
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--checkpoint-every", type=int, default=10)
+    ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--n-per-star", type=int, default=1 << 20)
     ap.add_argument("--thetas", default="0.3,0.5,0.7")
     ap.add_argument("--steps", type=int, default=200)
@@ -117,9 +154,12 @@ def main():
     if args.study == "binary":
         res = {"study": "binary", "runs": study_binary(args.n_per_star, thetas, args.steps,
                                                        args.dt, prec)}
-    else:
+    elif args.study == "force":
         res = {"study": "force", **study_force([int(v) for v in args.n_list.split(",")], thetas,
                                                prec)}
+    else:
+        res = {"study": "gradient", **study_gradient(args.n, args.steps, args.dt,
+                                                     args.checkpoint_every, args.theta, prec)}
     text = json.dumps(res, indent=1)
     if args.out:
         with open(args.out, "w") as f:
