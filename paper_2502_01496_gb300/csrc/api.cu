@@ -87,12 +87,15 @@ void phase_end(kdfmm_tree_s* t, int phase, cudaStream_t s) {
 static int grow_eval_buffers(kdfmm_tree_s* t, int64_t cap) {
   Lists& L = t->L;
   cudaFree(L.far_cnt); cudaFree(L.near_cnt); cudaFree(L.far_off); cudaFree(L.near_off);
-  L.far_cnt = L.near_cnt = nullptr;
+  cudaFree(L.heavy); cudaFree(L.seg_first);
+  L.far_cnt = L.near_cnt = L.heavy = L.seg_first = nullptr;
   L.far_off = L.near_off = nullptr;
   if (cudaMalloc(&L.far_cnt, (cap + 1) * sizeof(int32_t)) != cudaSuccess ||
       cudaMalloc(&L.near_cnt, (cap + 1) * sizeof(int32_t)) != cudaSuccess ||
       cudaMalloc(&L.far_off, (cap + 2) * sizeof(int64_t)) != cudaSuccess ||
-      cudaMalloc(&L.near_off, (cap + 2) * sizeof(int64_t)) != cudaSuccess)
+      cudaMalloc(&L.near_off, (cap + 2) * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&L.heavy, (cap + 1) * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&L.seg_first, (cap + 1) * sizeof(int32_t)) != cudaSuccess)
     return set_error(KDFMM_ERR_OOM, "interaction list offsets");
   // leaves that a walk skipped keep empty lists
   cudaMemset(L.far_cnt, 0, (cap + 1) * sizeof(int32_t));
@@ -257,7 +260,7 @@ static kdfmm_tree_s::GraphKey graph_key_of(const kdfmm_tree_s* t, const double* 
   k.x = x; k.m = m; k.h = h; k.a = a; k.phi = phi;
   k.n = t->n; k.cap_n = t->cap_n;
   k.cap_far = t->L.cap_far; k.cap_near = t->L.cap_near;
-  k.far_cap = t->L.far_cap; k.near_cap = t->L.near_cap;
+  k.far_cap = t->L.far_cap; k.near_cap = t->L.near_cap; k.seg_cap = t->L.seg_cap;
   k.n_sys = t->n_sys; k.cap_sys = t->cap_sys; k.min_nleaf = t->min_nleaf;
   k.soft_kind = t->p.soft_kind; k.precision = t->p.precision; k.r_kern = t->p.r_kern;
   k.expansion = t->p.expansion; k.walk = t->p.walk;
@@ -295,6 +298,7 @@ static void graph_capture(kdfmm_tree_s* t, const double* x, const double* m, con
   t->graph_levels = t->levels_used + 2;
   t->graph_leaves = (int32_t)std::min<int64_t>(t->n, (int64_t)t->nleaves + t->nleaves / 4 + 64);
   if (ensure_slots(t, t->graph_leaves)) return;
+  if (ensure_segments(t, segments_bound(t) + segments_bound(t) / 4)) return;
   const int32_t grid_eager = t->grid_leaves;
   const int64_t launches0 = t->launches;
   const bool timing = t->timing;
@@ -396,6 +400,7 @@ void kdfmm_tree_destroy(kdfmm_tree t) {
   cudaFree(t->counters); cudaFree(t->status); cudaFree(t->com_bound);
   cudaFree(t->L.far_cnt); cudaFree(t->L.near_cnt); cudaFree(t->L.far_off); cudaFree(t->L.near_off);
   cudaFree(t->L.far_idx); cudaFree(t->L.near_idx); cudaFree(t->L.near_np);
+  cudaFree(t->L.heavy); cudaFree(t->L.seg_first); cudaFree(t->L.seg_leaf); cudaFree(t->L.seg_part);
   cudaFree(t->mom_partial);
   cudaFree(t->sys_off); cudaFree(t->sys_theta); cudaFree(t->sys_eps); cudaFree(t->sys_nleaf);
   cudaFree(t->sys_root);
@@ -513,6 +518,7 @@ int kdfmm_fmm_accel(kdfmm_tree t, double* a, double* phi, void* stream) {
   if ((rc = dual ? run_dual_local(t, s) : run_m2l(t, s))) return rc;
   phase_end(t, KDFMM_PHASE_M2L, s);
   phase_begin(t, KDFMM_PHASE_P2P, s);
+  if ((rc = ensure_segments(t, segments_bound(t)))) return rc;
   if ((rc = run_p2p(t, a, phi, s))) return rc;
   phase_end(t, KDFMM_PHASE_P2P, s);
   t->evaluated = true;

@@ -43,6 +43,8 @@ enum : int {
   C_NA = 10,        // segments of the current phase-A level
   C_LEAVES = 11,    // leaves
   C_WORK = 12,      // dynamic work counter of the persistent subtree kernel
+  C_HEAVY = 13,     // leaves whose walk outgrew the per-thread budget (queued)
+  C_SEGS = 14,      // extra P2P segments of leaves with long near lists
 };
 
 // Grid of the grid-stride (persistent) kernels: blocks per SM x SMs of a GB300.
@@ -95,7 +97,23 @@ struct Lists {
   int64_t cap_far, cap_near;       // slot size per leaf (slot mode)
   bool exact;
   int64_t* near_np;                // device statistics of the walk (4)
+  int32_t* heavy;                  // leaves queued for the block-wide walk (nleaves)
+  // near lists longer than kSegEntries are split: segment 0 stays with the
+  // leaf, the others are work items of their own whose partial sums
+  // (seg_part, 32 targets x 4 doubles each) are added in segment order
+  int32_t* seg_first;              // per leaf: first extra segment, or -1
+  int32_t* seg_leaf;               // per extra segment: its leaf
+  double* seg_part;                // per extra segment: partial sums
+  int64_t seg_cap;                 // extra segments allocated
 };
+
+// Near entries per P2P segment.
+constexpr int kSegEntries = 256;
+
+// Extra segments of a near list of n entries.
+__host__ __device__ __forceinline__ int extra_segments(int64_t n) {
+  return n > kSegEntries ? (int)((n - 1) / kSegEntries) : 0;
+}
 
 }  // namespace kdfmm
 
@@ -190,14 +208,15 @@ struct kdfmm_tree_s {
   struct GraphKey {
     const void *x, *m, *h;
     void *a, *phi;
-    int64_t n, cap_n, cap_far, cap_near, far_cap, near_cap;
+    int64_t n, cap_n, cap_far, cap_near, far_cap, near_cap, seg_cap;
     int32_t n_sys, cap_sys, min_nleaf, soft_kind, precision, expansion, walk;
     double r_kern;
     bool operator==(const GraphKey& o) const {
       return x == o.x && m == o.m && h == o.h && a == o.a && phi == o.phi && n == o.n &&
              expansion == o.expansion && walk == o.walk &&
              cap_n == o.cap_n && cap_far == o.cap_far && cap_near == o.cap_near &&
-             far_cap == o.far_cap && near_cap == o.near_cap && n_sys == o.n_sys &&
+             far_cap == o.far_cap && near_cap == o.near_cap && seg_cap == o.seg_cap &&
+             n_sys == o.n_sys &&
              cap_sys == o.cap_sys && min_nleaf == o.min_nleaf && soft_kind == o.soft_kind &&
              precision == o.precision && r_kern == o.r_kern;
     }
@@ -410,6 +429,11 @@ int run_dual_walk(kdfmm_tree_s* t, cudaStream_t s);
 int run_dual_local(kdfmm_tree_s* t, cudaStream_t s);
 void free_dual(kdfmm_tree_s* t);
 int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s);
+// Extra P2P segments: storage for `need`, an upper bound from the last walk's
+// list sizes, and the plan (run by run_p2p; the adjoint reuses it).
+int ensure_segments(kdfmm_tree_s* t, int64_t need);
+int64_t segments_bound(const kdfmm_tree_s* t);
+int plan_segments(kdfmm_tree_s* t, cudaStream_t s);
 int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, cudaStream_t s);
 int momentum(const double* m, const double* v, int64_t n, double* out, double* scratch,
              cudaStream_t s);

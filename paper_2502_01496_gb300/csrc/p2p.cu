@@ -12,7 +12,12 @@
 //
 // One warp per target leaf.  A leaf of n_t <= 32 targets uses K = 32 / n_t
 // source slices: lane = target + n_t * slice, slice k takes sources k, k+K, ...
-// of every near leaf, and the slices are combined at the end.
+// of every near leaf, and the slices are combined at the end.  A near list
+// longer than kSegEntries leaves (a large leaf in the sparse outskirts of a
+// centrally condensed system can have most of the system in it) is split
+// into segments of kSegEntries: the leaf's warp takes the first, the others
+// are separate work items, and their partial sums are added afterwards in
+// segment order, so the result does not depend on scheduling.
 //
 // Mixed mode: positions are float32 offsets from each particle's own leaf
 // centre of mass; the target is shifted by the difference of the two leaf
@@ -52,6 +57,13 @@ struct P2PArgs {
   const double* sys_eps;     // Plummer softening length of each system
   double* a;
   double* phi;
+  // near lists longer than kSegEntries: segment 0 is the leaf's own work
+  // item, the others (counters[C_SEGS], at most seg_cap) are items after the
+  // leaves, whose partial sums seg_part k_seg_combine adds in segment order
+  const int32_t* seg_first;
+  const int32_t* seg_leaf;
+  double* seg_part;
+  int64_t seg_cap;
 };
 
 // M4 cubic spline, q = r/h < 2: F(q)/q^3 and P(q) (qi = 1/q).
@@ -269,7 +281,12 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
   __shared__ float4 s_toff[kP2PWarps][32];                          // and offset to the target com
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nleaves = min(A.counters[C_LEAVES], A.max_leaves);
-  for (int k = blockIdx.x * kP2PWarps + warp; k < nleaves; k += gridDim.x * kP2PWarps) {
+  const int nitems = nleaves + (int)min((int64_t)A.counters[C_SEGS], A.seg_cap);
+  for (int item = blockIdx.x * kP2PWarps + warp; item < nitems; item += gridDim.x * kP2PWarps) {
+  const bool seg = item >= nleaves;
+  const int g = item - nleaves;
+  const int k = seg ? A.seg_leaf[g] : item;
+  if (k < 0) continue;
   float4* sp = s_pos[warp];
   float4* sk = s_ker[M4 ? warp : 0];
   int* tb = s_tbeg[warp];
@@ -288,15 +305,17 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
   const double eps = A.sys_eps[A.leaf_sys[k]];
   const float eps2f = (float)(eps * eps);
   float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, azh = 0.f, azl = 0.f, ph_ = 0.f, pl = 0.f;
-  {
+  if (!seg) {
     float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;
     if (act)
       near_leaf32<SOFT, true>(A, fa, nt, sl, K, t, xa.x, xa.y, xa.z, hi, eps2f, fx, fy, fz, fp);
     df_add(axh, axl, fx); df_add(ayh, ayl, fy); df_add(azh, azl, fz); df_add(ph_, pl, fp);
   }
   const unsigned full = 0xffffffffu, lt = (1u << lane) - 1u;
-  const int64_t e1 = A.near_off[k] + min((int64_t)A.near_cnt[k], A.cap_near);
-  for (int64_t e = A.near_off[k]; e < e1;) {
+  const int64_t nall = min((int64_t)A.near_cnt[k], A.cap_near);
+  const int64_t sidx = seg ? (int64_t)(g - A.seg_first[k] + 1) : 0;
+  const int64_t e1 = A.near_off[k] + min(nall, (sidx + 1) * kSegEntries);
+  for (int64_t e = A.near_off[k] + sidx * kSegEntries; e < e1;) {
     // up to 32 candidate leaves, one per lane
     const int64_t my = e + lane;
     int cnt = 0, first = 0;
@@ -445,6 +464,14 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
     }
   }
   if (sl != 0 || !act) continue;
+  if (seg) {
+    double* P = A.seg_part + (int64_t)g * 128 + 4 * t;
+    P[0] = (double)axh + (double)axl;
+    P[1] = (double)ayh + (double)ayl;
+    P[2] = (double)azh + (double)azl;
+    P[3] = (double)ph_ + (double)pl;
+    continue;
+  }
   const float* C = A.lexp32 + 24 * (int64_t)k;
   float tx, ty, tz, tp_;
   l2p_tail<float>(C, xa.x, xa.y, xa.z, tx, ty, tz, tp_);
@@ -463,8 +490,13 @@ template <int SOFT>
 __global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
   const int lane = threadIdx.x & 31;
   const int nleaves = min(A.counters[C_LEAVES], A.max_leaves);
-  for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < nleaves;
-       k += (int)((gridDim.x * blockDim.x) >> 5)) {
+  const int nitems = nleaves + (int)min((int64_t)A.counters[C_SEGS], A.seg_cap);
+  for (int item = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); item < nitems;
+       item += (int)((gridDim.x * blockDim.x) >> 5)) {
+  const bool seg = item >= nleaves;
+  const int g = item - nleaves;
+  const int k = seg ? A.seg_leaf[g] : item;
+  if (k < 0) continue;
   const int a = A.leaf_cells[k];
   const int fa = A.cfirst[a], nt = A.ccount[a];
   const int K = 32 / nt;
@@ -475,7 +507,10 @@ __global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
   const double eps = A.sys_eps[A.leaf_sys[k]];
   const double eps2 = eps * eps;
   double fx = 0.0, fy = 0.0, fz = 0.0, fp = 0.0;
-  const int64_t e0 = A.near_off[k], e1 = e0 + min((int64_t)A.near_cnt[k], A.cap_near);
+  const int64_t nall = min((int64_t)A.near_cnt[k], A.cap_near);
+  const int64_t sidx = seg ? (int64_t)(g - A.seg_first[k] + 1) : 0;
+  const int64_t e0 = A.near_off[k] + sidx * kSegEntries;
+  const int64_t e1 = A.near_off[k] + min(nall, (sidx + 1) * kSegEntries);
   if (act) {
     for (int64_t e = e0; e < e1; ++e) {
       const int b = A.near_idx[e];
@@ -495,6 +530,11 @@ __global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
     if (sl == 0) { fx += bx; fy += by; fz += bz; fp += bp; }
   }
   if (sl != 0 || !act) continue;
+  if (seg) {
+    double* P = A.seg_part + (int64_t)g * 128 + 4 * t;
+    P[0] = fx; P[1] = fy; P[2] = fz; P[3] = fp;
+    continue;
+  }
   const double* C = A.lexp64 + 20 * (int64_t)k;
   const double x = xi - A.cx[a], y = yi - A.cy[a], z = zi - A.cz[a];
   double tx, ty, tz, tp_;
@@ -507,9 +547,105 @@ __global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
   }
 }
 
+// Reserves the extra segments of every leaf (any order: a leaf's segments
+// are contiguous and combined in segment order).  More than seg_cap flags
+// ST_LISTS and drops the leaf's extra segments (the evaluation is redone);
+// their entries below seg_cap are marked -1, which every consumer skips.
+__global__ void k_seg_plan(const int32_t* __restrict__ near_cnt, int64_t cap_near,
+                           int max_leaves, int32_t* counters, int32_t* seg_first,
+                           int32_t* seg_leaf, int64_t seg_cap, int32_t* status) {
+  const int nleaves = min(counters[C_LEAVES], max_leaves);
+  KD_GRID_STRIDE(k, nleaves) {
+    const int x = extra_segments(min((int64_t)near_cnt[k], cap_near));
+    int first = -1;
+    if (x > 0) {
+      const int base = atomicAdd(&counters[C_SEGS], x);
+      if ((int64_t)base + x <= seg_cap) {
+        first = base;
+        for (int q = 0; q < x; ++q) seg_leaf[base + q] = k;
+      } else {
+        atomicOr(status, ST_LISTS);
+        for (int q = 0; q < x && (int64_t)base + q < seg_cap; ++q) seg_leaf[base + q] = -1;
+      }
+    }
+    seg_first[k] = first;
+  }
+}
+
+// Adds the extra segments' partial sums to a and phi (caller order), warp
+// per leaf (the warp of its first extra segment), lane per target.
+__global__ void k_seg_combine(P2PArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int nseg = (int)min((int64_t)A.counters[C_SEGS], A.seg_cap);
+  for (int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); g < nseg;
+       g += (int)((gridDim.x * blockDim.x) >> 5)) {
+    const int k = A.seg_leaf[g];
+    if (k < 0) continue;
+    const int f = A.seg_first[k];
+    if (g != f) continue;
+    const int a = A.leaf_cells[k];
+    if (lane >= A.ccount[a]) continue;
+    const int x = extra_segments(min((int64_t)A.near_cnt[k], A.cap_near));
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int q = 0; q < x; ++q) {
+      const double* P = A.seg_part + (int64_t)(f + q) * 128 + 4 * lane;
+      s0 += P[0]; s1 += P[1]; s2 += P[2]; s3 += P[3];
+    }
+    const int64_t ci = A.tp.idx[A.cfirst[a] + lane];
+    A.a[3 * ci + 0] += s0;
+    A.a[3 * ci + 1] += s1;
+    A.a[3 * ci + 2] += s2;
+    if (A.phi) A.phi[ci] += s3;
+  }
+}
+
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
+
+int ensure_segments(kdfmm_tree_s* t, int64_t need) {
+  Lists& L = t->L;
+  if (L.seg_cap >= need && L.seg_leaf != nullptr) return KDFMM_OK;
+  // the plan of the last evaluation is kept (the adjoint reuses it)
+  const int64_t cap = std::max<int64_t>(need, 64);
+  int32_t* leaf = nullptr;
+  double* part = nullptr;
+  if (cudaMalloc(&leaf, (size_t)cap * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&part, (size_t)cap * 128 * sizeof(double)) != cudaSuccess) {
+    cudaFree(leaf);
+    cudaGetLastError();
+    return set_error(KDFMM_ERR_OOM, "P2P segments (%lld)", (long long)cap);
+  }
+  if (L.seg_leaf != nullptr && L.seg_cap > 0 &&
+      cudaMemcpy(leaf, L.seg_leaf, (size_t)L.seg_cap * sizeof(int32_t), cudaMemcpyDeviceToDevice) !=
+          cudaSuccess) {
+    cudaFree(leaf);
+    cudaFree(part);
+    return check_cuda(cudaGetLastError(), "segment copy");
+  }
+  cudaFree(L.seg_leaf);
+  cudaFree(L.seg_part);
+  L.seg_leaf = leaf;
+  L.seg_part = part;
+  L.seg_cap = cap;
+  return KDFMM_OK;
+}
+
+int64_t segments_bound(const kdfmm_tree_s* t) {
+  const Lists& L = t->L;
+  const int64_t entries = L.exact ? L.near_cap : t->host_stats[KDFMM_STAT_NNEAR];
+  return entries / kSegEntries + 64;
+}
+
+int plan_segments(kdfmm_tree_s* t, cudaStream_t s) {
+  const int gl = std::max(t->grid_leaves, 1);
+  cudaMemsetAsync(t->counters + C_SEGS, 0, sizeof(int32_t), s);
+  k_seg_plan<<<std::min<unsigned>(blocks_for(gl, 256), kGridBlocks), 256, 0, s>>>(
+      t->L.near_cnt, t->L.exact ? INT64_MAX : t->L.cap_near, gl, t->counters, t->L.seg_first,
+      t->L.seg_leaf, t->L.seg_cap, t->status);
+  t->launches += 1;
+  return check_cuda(cudaGetLastError(), "segment plan");
+}
 
 int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s) {
   P2PArgs A{};
@@ -535,6 +671,12 @@ int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s) {
   A.sys_eps = t->sys_eps;
   A.a = a;
   A.phi = phi;
+  A.seg_first = t->L.seg_first;
+  A.seg_leaf = t->L.seg_leaf;
+  A.seg_part = t->L.seg_part;
+  A.seg_cap = t->L.seg_cap;
+  int rc = plan_segments(t, s);
+  if (rc) return rc;
   const int gl = std::max(t->grid_leaves, 1);
   const unsigned g = blocks_for((int64_t)gl * 32, 256);
   const bool m4 = t->p.soft_kind == KDFMM_SOFT_M4;
@@ -546,7 +688,8 @@ int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s) {
     if (m4) k_p2p_fp64<KDFMM_SOFT_M4><<<g, 256, 0, s>>>(A);
     else k_p2p_fp64<KDFMM_SOFT_PLUMMER><<<g, 256, 0, s>>>(A);
   }
-  t->launches += 1;
+  k_seg_combine<<<152 * 2, 256, 0, s>>>(A);
+  t->launches += 2;
   return check_cuda(cudaGetLastError(), "p2p launch");
 }
 

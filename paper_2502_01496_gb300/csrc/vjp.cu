@@ -194,6 +194,12 @@ struct VjpArgs {
   double* msrc;                         // P2P source-side part of m_bar (N, atomics)
   double* cbar;                         // per leaf: 20 expansion cotangents
   double* cell_bar;                     // per cell: M_bar, com_bar (3), Q_bar (6)
+  // the evaluation's split of long near lists (segment items after the
+  // leaves; their target-side partial sums are added in segment order)
+  const int32_t* counters;
+  const int32_t *seg_first, *seg_leaf;
+  double* seg_part;
+  int64_t seg_cap;
 };
 
 __global__ void k_gather_abar(const double* __restrict__ abar, VjpArgs V) {
@@ -397,9 +403,14 @@ __device__ __forceinline__ void pair_fg(int kind, S r2, S eps2, S hi, S hj, S& f
 template <class S>
 __global__ void k_vjp_p2p(VjpArgs V) {
   const unsigned full = 0xffffffffu;
-  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (k >= V.nleaves) return;
+  const int nitems = V.nleaves + (int)min((int64_t)V.counters[C_SEGS], V.seg_cap);
+  for (int item = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); item < nitems;
+       item += (int)((gridDim.x * blockDim.x) >> 5)) {
+  const bool seg = item >= V.nleaves;
+  const int g = item - V.nleaves;
+  const int k = seg ? V.seg_leaf[g] : item;
+  if (k < 0) continue;
   const int a = V.leaf_cells[k];
   const int fa = V.c.first[a], nt = V.c.count[a];
   const int K = 32 / nt, t = lane % nt, sl = lane / nt;
@@ -409,8 +420,10 @@ __global__ void k_vjp_p2p(VjpArgs V) {
   const S bS[3] = {(S)V.ab[3 * pi], (S)V.ab[3 * pi + 1], (S)V.ab[3 * pi + 2]};
   const double eps = V.sys_eps[V.leaf_sys[k]], eps2 = eps * eps;
   double gx = 0.0, gy = 0.0, gz = 0.0;
-  const int64_t e0 = V.near_off[k];
-  const int nn = (int)min((int64_t)V.near_cnt[k], V.cap_near);
+  const int64_t nall = min((int64_t)V.near_cnt[k], V.cap_near);
+  const int64_t sidx = seg ? (int64_t)(g - V.seg_first[k] + 1) : 0;
+  const int64_t e0 = V.near_off[k] + sidx * kSegEntries;
+  const int nn = (int)(min(nall, (sidx + 1) * kSegEntries) - sidx * kSegEntries);
   for (int e = 0; e < nn; ++e) {
     const int bc = V.near_idx[e0 + e];
     const int fb = V.c.first[bc], nb = V.c.count[bc];
@@ -454,9 +467,41 @@ __global__ void k_vjp_p2p(VjpArgs V) {
     if (sl == 0) { gx += ox; gy += oy; gz += oz; }
   }
   if (act && sl == 0) {
-    V.xbar[3 * pi] += gx;
-    V.xbar[3 * pi + 1] += gy;
-    V.xbar[3 * pi + 2] += gz;
+    if (seg) {
+      double* P = V.seg_part + (int64_t)g * 128 + 4 * t;
+      P[0] = gx; P[1] = gy; P[2] = gz;
+    } else {
+      V.xbar[3 * pi] += gx;
+      V.xbar[3 * pi + 1] += gy;
+      V.xbar[3 * pi + 2] += gz;
+    }
+  }
+  }
+}
+
+// Adds the extra segments' target-side sums to x_bar, warp per leaf (the
+// warp of its first extra segment), lane per target, in segment order.
+__global__ void k_vjp_seg_combine(VjpArgs V) {
+  const int lane = threadIdx.x & 31;
+  const int nseg = (int)min((int64_t)V.counters[C_SEGS], V.seg_cap);
+  for (int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); g < nseg;
+       g += (int)((gridDim.x * blockDim.x) >> 5)) {
+    const int k = V.seg_leaf[g];
+    if (k < 0) continue;
+    const int f = V.seg_first[k];
+    if (g != f) continue;
+    const int a = V.leaf_cells[k];
+    if (lane >= V.c.count[a]) continue;
+    const int x = extra_segments(min((int64_t)V.near_cnt[k], V.cap_near));
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int q = 0; q < x; ++q) {
+      const double* P = V.seg_part + (int64_t)(f + q) * 128 + 4 * lane;
+      s0 += P[0]; s1 += P[1]; s2 += P[2];
+    }
+    const int64_t pi = (int64_t)V.c.first[a] + lane;
+    V.xbar[3 * pi] += s0;
+    V.xbar[3 * pi + 1] += s1;
+    V.xbar[3 * pi + 2] += s2;
   }
 }
 
@@ -545,6 +590,11 @@ int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, 
   V.far_off = t->L.far_off; V.near_off = t->L.near_off;
   V.cap_far = t->L.exact ? INT64_MAX : t->L.cap_far;
   V.cap_near = t->L.exact ? INT64_MAX : t->L.cap_near;
+  V.counters = t->counters;
+  V.seg_first = t->L.seg_first;
+  V.seg_leaf = t->L.seg_leaf;
+  V.seg_part = t->L.seg_part;
+  V.seg_cap = t->L.seg_cap;
   double* dp = reinterpret_cast<double*>(buf);
   V.ab = dp; dp += 3 * n;
   V.xbar = dp; dp += 3 * n;
@@ -567,9 +617,10 @@ int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, 
     else k_vjp_m2l<false, double><<<gw, 128, 0, s>>>(V);
     k_vjp_p2p<double><<<gw, 128, 0, s>>>(V);
   }
+  k_vjp_seg_combine<<<152 * 2, 256, 0, s>>>(V);
   k_vjp_moments<<<blocks_for(nl, 128), 128, 0, s>>>(V);
   k_scatter_bar<<<blocks_for(n, 256), 256, 0, s>>>(V, x_bar, m_bar);
-  t->launches += 6;
+  t->launches += 7;
   rc = check_cuda(cudaGetLastError(), "adjoint launch");
   cudaFreeAsync(buf, s);
   return rc;

@@ -47,6 +47,9 @@ struct WalkArgs {
   bool exact;                      // exact mode: far_off / near_off are given, no limit
   int32_t* maxc;                   // [0] longest far list, [1] longest near list
   unsigned long long* stats;       // [0] P2P interactions, [1] float64 decisions, [2] far, [3] near
+  int budget;                      // cells one thread visits before handing its leaf on
+  int32_t* heavy;                  // queue of the leaves handed on
+  int32_t* heavy_n;                // its length (counters[C_HEAVY])
 };
 
 __device__ __forceinline__ bool open_exact(double ax, double ay, double az, double sa, double ha,
@@ -82,7 +85,10 @@ __device__ __forceinline__ int open_filter(float4 a, float ha, float4 b, float h
 // the leaf (entries beyond the capacity are counted, not stored; the host
 // then grows the slots and walks again, or switches to exact mode).  Exact
 // mode: the counts of a previous pass, scanned, give each leaf's start.
-__global__ void __launch_bounds__(128) k_walk(WalkArgs W) {
+// A leaf whose walk visits more than W.budget cells (a large leaf in the
+// sparse outskirts of a centrally condensed system opens most of the tree)
+// is queued for k_walk_heavy, which redoes it with a whole block.
+__global__ void __launch_bounds__(128, 10) k_walk(WalkArgs W) {
   // the grid covers slot_leaves leaves; more leaves than slots is flagged and
   // the evaluation is redone by the host
   const int nleaves = W.counters[C_LEAVES];
@@ -118,7 +124,12 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs W) {
   int nf = 0, nn = 0, nex = 0;
   long long np = 0;
   int i = W.sys_root[sys];              // the walk stays inside the leaf's own tree
+  int visits = 0;
   while (i < i_end) {
+    if (++visits > W.budget) {
+      W.heavy[atomicAdd(W.heavy_n, 1)] = k;
+      return;
+    }
     const float4 wb = W.walk[i];
     const float2 w2 = W.walk2[i];
     const int skip = __float_as_int(w2.y);
@@ -153,7 +164,193 @@ __global__ void __launch_bounds__(128) k_walk(WalkArgs W) {
   }
 }
 
+// Block-wide walk of the queued leaves.  The depth-first walk visits cell i
+// unless a cell p < i with i < skip(p) -- an ancestor of i in pre-order --
+// was closed; so with every cell of the system decided at once, i is visited
+// iff the largest skip pointer of the closed cells before i does not exceed
+// i (a prefix maximum).  A visited closed cell joins the far list, a visited
+// opened leaf the near list; a block scan keeps them in ascending id, as the
+// thread walk emits them.  Tiles of kHeavyTile cells advance past the subtrees
+// closed so far, so closed regions are not read.
+constexpr int kHeavyThreads = 256;
+constexpr int kHeavyPer = 4;                        // consecutive cells per thread
+constexpr int kHeavyTile = kHeavyThreads * kHeavyPer;
+constexpr int kHeavyWarps = kHeavyThreads / 32;
+constexpr int kHeavyGrid = 152 * 2;
+
+// Exclusive block scan (maximum) of v; *total gets the block's maximum.
+__device__ __forceinline__ int block_excl_max(int v, int* total, int* sh) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(full, inc, o);
+    if (lane >= o) inc = max(inc, u);
+  }
+  int ex = __shfl_up_sync(full, inc, 1);
+  if (lane == 0) ex = 0;
+  if (lane == 31) sh[w] = inc;
+  __syncthreads();
+  int pre = 0, tot = 0;
+#pragma unroll
+  for (int q = 0; q < kHeavyWarps; ++q) {
+    if (q < w) pre = max(pre, sh[q]);
+    tot = max(tot, sh[q]);
+  }
+  __syncthreads();
+  *total = tot;
+  return max(pre, ex);
+}
+
+// Exclusive block scan (sum) of (a, b); *ta, *tb get the block's sums.
+__device__ __forceinline__ int2 block_excl_sum2(int a, int b, int* ta, int* tb, int2* sh) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int ua = __shfl_up_sync(full, ia, o), ub = __shfl_up_sync(full, ib, o);
+    if (lane >= o) { ia += ua; ib += ub; }
+  }
+  if (lane == 31) sh[w] = make_int2(ia, ib);
+  __syncthreads();
+  int pa = 0, pb = 0, sa = 0, sb = 0;
+#pragma unroll
+  for (int q = 0; q < kHeavyWarps; ++q) {
+    const int2 v = sh[q];
+    if (q < w) { pa += v.x; pb += v.y; }
+    sa += v.x; sb += v.y;
+  }
+  __syncthreads();
+  *ta = sa;
+  *tb = sb;
+  return make_int2(pa + ia - a, pb + ib - b);
+}
+
+__global__ void __launch_bounds__(kHeavyThreads) k_walk_heavy(WalkArgs W) {
+  __shared__ int sh_max[kHeavyWarps];
+  __shared__ int2 sh_sum[kHeavyWarps];
+  __shared__ long long sh_np[kHeavyWarps];
+  __shared__ int sh_nex[kHeavyWarps];
+  const int nq = *W.heavy_n;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int k = W.heavy[q];
+    const int a = W.leaf_cells[k];
+    const float4 wa = W.walk[a];
+    const float ha = W.walk2[a].x;
+    const double ax = W.cx[a], ay = W.cy[a], az = W.cz[a], sa = W.s[a], ha64 = W.hmax[a];
+    const float bound = *W.com_bound;
+    const int sys = W.leaf_sys[k];
+    const double theta = W.sys_theta[sys];
+    const int i0 = W.sys_root[sys], i_end = W.sys_root[sys + 1];
+    const float thf = (float)theta, rkf = (float)W.r_kern;
+    const bool always = theta == 0.0;
+    const int64_t fo = W.exact ? W.far_off[k] : (int64_t)k * W.cap_far;
+    const int64_t no = W.exact ? W.near_off[k] : (int64_t)k * W.cap_near;
+    int32_t* far = W.far_idx + fo;
+    int32_t* near = W.near_idx + no;
+    const int64_t cap_far = W.exact ? INT64_MAX : W.cap_far;
+    const int64_t cap_near = W.exact ? INT64_MAX : W.cap_near;
+    int nf = 0, nn = 0, carry = 0, nex = 0;
+    long long np = 0;
+    for (int t0 = i0; t0 < i_end;) {
+      const int c0 = t0 + kHeavyPer * (int)threadIdx.x;
+      int o[kHeavyPer], sk[kHeavyPer];
+      bool ex[kHeavyPer];
+      int tmax = 0;
+#pragma unroll
+      for (int j = 0; j < kHeavyPer; ++j) {
+        const int c = c0 + j;
+        o[j] = 1;
+        sk[j] = 0;
+        ex[j] = false;
+        if (c < i_end) {
+          const float4 wb = W.walk[c];
+          const float2 w2 = W.walk2[c];
+          sk[j] = __float_as_int(w2.y);
+          o[j] = always ? 1 : open_filter(wa, ha, wb, w2.x, thf, rkf, bound);
+          if (o[j] < 0) {
+            o[j] = open_exact(ax, ay, az, sa, ha64, W.cx[c], W.cy[c], W.cz[c], W.s[c], W.hmax[c],
+                              theta, W.r_kern);
+            ex[j] = true;
+          }
+          if (!o[j]) tmax = max(tmax, sk[j]);
+        }
+      }
+      int tile_max;
+      int pre = max(carry, block_excl_max(tmax, &tile_max, sh_max));
+      int mf = 0, mn = 0;
+      bool ef[kHeavyPer], en[kHeavyPer];
+#pragma unroll
+      for (int j = 0; j < kHeavyPer; ++j) {
+        const int c = c0 + j;
+        const bool vis = c < i_end && pre <= c;
+        ef[j] = vis && !o[j];
+        en[j] = vis && o[j] && sk[j] == c + 1;
+        mf += ef[j];
+        mn += en[j];
+        if (en[j]) np += W.count[c];
+        if (vis && ex[j]) ++nex;
+        if (c < i_end && !o[j]) pre = max(pre, sk[j]);
+      }
+      int tf, tn;
+      const int2 pos = block_excl_sum2(mf, mn, &tf, &tn, sh_sum);
+      int pf = nf + pos.x, pn = nn + pos.y;
+#pragma unroll
+      for (int j = 0; j < kHeavyPer; ++j) {
+        if (ef[j]) { if (pf < cap_far) far[pf] = c0 + j; ++pf; }
+        if (en[j]) { if (pn < cap_near) near[pn] = c0 + j; ++pn; }
+      }
+      nf += tf;
+      nn += tn;
+      carry = max(carry, tile_max);
+      t0 = max(t0 + kHeavyTile, carry);
+    }
+    // block sums of the pair count and the float64 decisions
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+      np += __shfl_xor_sync(full, np, o2);
+      nex += __shfl_xor_sync(full, nex, o2);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { sh_np[w] = np; sh_nex[w] = nex; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long npt = 0;
+      int nxt = 0;
+      for (int q2 = 0; q2 < kHeavyWarps; ++q2) { npt += sh_np[q2]; nxt += sh_nex[q2]; }
+      if (!W.exact) {
+        W.far_off[k] = fo;
+        W.near_off[k] = no;
+      }
+      W.far_cnt[k] = nf;
+      W.near_cnt[k] = nn;
+      atomicMax(&W.maxc[0], nf);
+      atomicMax(&W.maxc[1], nn);
+      const long long na = W.count[a];
+      atomicAdd(&W.stats[0], (unsigned long long)(na * npt - na));
+      atomicAdd(&W.stats[2], (unsigned long long)nf);
+      atomicAdd(&W.stats[3], (unsigned long long)nn);
+      if (nxt) atomicAdd(&W.stats[1], (unsigned long long)nxt);
+    }
+    __syncthreads();
+  }
+}
+
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// Cells one thread walks before its leaf goes to the block-wide walk
+// (KDFMM_WALK_BUDGET overrides it; the lists do not depend on it).
+static int walk_budget() {
+  const char* v = getenv("KDFMM_WALK_BUDGET");
+  if (v != nullptr) {
+    const long b = strtol(v, nullptr, 10);
+    if (b >= 1 && b <= INT_MAX) return (int)b;
+  }
+  return 4096;
+}
 
 }  // namespace
 
@@ -212,6 +409,9 @@ static WalkArgs walk_args(kdfmm_tree_s* t) {
   W.near_off = L.near_off;
   W.maxc = t->counters + C_MAXFAR;
   W.stats = reinterpret_cast<unsigned long long*>(L.near_np);
+  W.budget = walk_budget();
+  W.heavy = L.heavy;
+  W.heavy_n = t->counters + C_HEAVY;
   return W;
 }
 
@@ -227,8 +427,10 @@ static void walk_launch(kdfmm_tree_s* t, WalkArgs W, bool exact, int64_t cf, int
   W.slot_leaves = slot_leaves;
   cudaMemsetAsync(L.near_np, 0, 4 * sizeof(int64_t), s);
   cudaMemsetAsync(t->counters + C_MAXFAR, 0, 2 * sizeof(int32_t), s);
+  cudaMemsetAsync(t->counters + C_HEAVY, 0, sizeof(int32_t), s);
   k_walk<<<blocks_for(std::max(slot_leaves, 1), 128), 128, 0, s>>>(W);
-  t->launches += 1;
+  k_walk_heavy<<<kHeavyGrid, kHeavyThreads, 0, s>>>(W);
+  t->launches += 2;
 }
 
 int ensure_slots(kdfmm_tree_s* t, int slot_leaves) {

@@ -105,6 +105,8 @@ VJP_CASES = {
     "polytrope_m4_fp64": (lambda: W.polytrope_binary(1000, W.seed_for(0, 22)), 0.6, 16, FP64, 1e-8),
     "clumps_leaf32_fp64": (lambda: W.uniform_clumps(1201, W.seed_for(0, 23)), 0.4, 32, FP64, 1e-8),
     "polytrope_m4_mixed": (lambda: W.polytrope_binary(1000, W.seed_for(0, 24)), 0.6, 16, MIXED, 1e-5),
+    # near lists of the outskirts' leaves span several P2P segments
+    "plummer4096_segments_fp64": (lambda: W.plummer(4096, W.seed_for(0, 25)), 0.5, 16, FP64, 1e-8),
 }
 
 
