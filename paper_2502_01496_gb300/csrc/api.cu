@@ -261,6 +261,7 @@ static kdfmm_tree_s::GraphKey graph_key_of(const kdfmm_tree_s* t, const double* 
   k.n = t->n; k.cap_n = t->cap_n;
   k.cap_far = t->L.cap_far; k.cap_near = t->L.cap_near;
   k.far_cap = t->L.far_cap; k.near_cap = t->L.near_cap; k.seg_cap = t->L.seg_cap;
+  k.temp_cap = t->L.temp_cap; k.arena = t->L.arena; k.arena_grid = t->L.arena_grid;
   k.n_sys = t->n_sys; k.cap_sys = t->cap_sys; k.min_nleaf = t->min_nleaf;
   k.soft_kind = t->p.soft_kind; k.precision = t->p.precision; k.r_kern = t->p.r_kern;
   k.expansion = t->p.expansion; k.walk = t->p.walk;
@@ -289,7 +290,7 @@ static void graph_capture(kdfmm_tree_s* t, const double* x, const double* m, con
     cudaGetLastError();
     return;
   }
-  if (t->L.exact) return;                 // exact lists need the host between two walks
+  if (t->L.exact && !t->L.arena) return;  // lists made by the host between passes
   if (!t->capture_stream &&
       cudaStreamCreateWithFlags(&t->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -297,7 +298,7 @@ static void graph_capture(kdfmm_tree_s* t, const double* x, const double* m, con
   }
   t->graph_levels = t->levels_used + 2;
   t->graph_leaves = (int32_t)std::min<int64_t>(t->n, (int64_t)t->nleaves + t->nleaves / 4 + 64);
-  if (ensure_slots(t, t->graph_leaves)) return;
+  if (t->L.arena ? ensure_arena(t, t->graph_leaves, 1.25) : ensure_slots(t, t->graph_leaves)) return;
   if (ensure_segments(t, segments_bound(t) + segments_bound(t) / 4)) return;
   const int32_t grid_eager = t->grid_leaves;
   const int64_t launches0 = t->launches;
@@ -342,7 +343,7 @@ static int graph_replay(kdfmm_tree_s* t, cudaStream_t s) {
   if (st & ST_NONFINITE)
     return set_error(KDFMM_ERR_NONFINITE, "non-finite position or non-positive mass / h");
   if ((st & (ST_UNFINISHED | ST_LISTS | ST_CAPACITY | ST_INTERNAL)) ||
-      hc[C_MAXFAR] > t->L.cap_far || hc[C_MAXNEAR] > t->L.cap_near)
+      (!t->L.arena && (hc[C_MAXFAR] > t->L.cap_far || hc[C_MAXNEAR] > t->L.cap_near)))
     return 1;
   t->ncells = hc[C_CELLS];
   t->nleaves = hc[C_LEAVES];
@@ -401,6 +402,7 @@ void kdfmm_tree_destroy(kdfmm_tree t) {
   cudaFree(t->L.far_cnt); cudaFree(t->L.near_cnt); cudaFree(t->L.far_off); cudaFree(t->L.near_off);
   cudaFree(t->L.far_idx); cudaFree(t->L.near_idx); cudaFree(t->L.near_np);
   cudaFree(t->L.heavy); cudaFree(t->L.seg_first); cudaFree(t->L.seg_leaf); cudaFree(t->L.seg_part);
+  cudaFree(t->L.temp);
   cudaFree(t->mom_partial);
   cudaFree(t->sys_off); cudaFree(t->sys_theta); cudaFree(t->sys_eps); cudaFree(t->sys_nleaf);
   cudaFree(t->sys_root);

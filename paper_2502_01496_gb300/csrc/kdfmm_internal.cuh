@@ -95,7 +95,11 @@ struct Lists {
   int32_t *far_idx, *near_idx;
   int64_t far_cap, near_cap;       // allocated entries
   int64_t cap_far, cap_near;       // slot size per leaf (slot mode)
-  bool exact;
+  bool exact;                      // offsets are per leaf, counts unlimited (arena or dual walk)
+  bool arena;                      // leaf walk into reserved room (one pass, see walk.cu)
+  int32_t* temp;                   // arena walk: per-thread scratch
+  int64_t temp_cap;                // its entries
+  int32_t arena_grid;              // blocks of the arena walk
   int64_t* near_np;                // device statistics of the walk (4)
   int32_t* heavy;                  // leaves queued for the block-wide walk (nleaves)
   // near lists longer than kSegEntries are split: segment 0 stays with the
@@ -208,14 +212,16 @@ struct kdfmm_tree_s {
   struct GraphKey {
     const void *x, *m, *h;
     void *a, *phi;
-    int64_t n, cap_n, cap_far, cap_near, far_cap, near_cap, seg_cap;
-    int32_t n_sys, cap_sys, min_nleaf, soft_kind, precision, expansion, walk;
+    int64_t n, cap_n, cap_far, cap_near, far_cap, near_cap, seg_cap, temp_cap;
+    int32_t n_sys, cap_sys, min_nleaf, soft_kind, precision, expansion, walk, arena_grid;
+    bool arena;
     double r_kern;
     bool operator==(const GraphKey& o) const {
       return x == o.x && m == o.m && h == o.h && a == o.a && phi == o.phi && n == o.n &&
              expansion == o.expansion && walk == o.walk &&
              cap_n == o.cap_n && cap_far == o.cap_far && cap_near == o.cap_near &&
              far_cap == o.far_cap && near_cap == o.near_cap && seg_cap == o.seg_cap &&
+             temp_cap == o.temp_cap && arena == o.arena && arena_grid == o.arena_grid &&
              n_sys == o.n_sys &&
              cap_sys == o.cap_sys && min_nleaf == o.min_nleaf && soft_kind == o.soft_kind &&
              precision == o.precision && r_kern == o.r_kern;
@@ -420,6 +426,9 @@ int run_walk(kdfmm_tree_s* t, cudaStream_t s);
 // (ensure_slots first; overflow is flagged in the status word)
 int ensure_slots(kdfmm_tree_s* t, int slot_leaves);
 int walk_fixed(kdfmm_tree_s* t, int slot_leaves, cudaStream_t s);
+// Arena mode: list buffers for `extra` times the last walk's entries and the
+// scratch of an arena walk over `leaves` leaves (before a capture).
+int ensure_arena(kdfmm_tree_s* t, int leaves, double extra);
 int run_m2l(kdfmm_tree_s* t, cudaStream_t s);
 int run_m2l_cells(kdfmm_tree_s* t, const int32_t* far_cnt, const int64_t* far_off,
                   const int32_t* far_idx, float* out32, double* out64, cudaStream_t s);

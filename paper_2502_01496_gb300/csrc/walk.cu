@@ -44,7 +44,10 @@ struct WalkArgs {
   int64_t *far_off, *near_off;     // where leaf k's lists start
   int32_t *far_idx, *near_idx;
   int64_t cap_far, cap_near;       // slot mode: entries per leaf (k * cap is the start)
-  bool exact;                      // exact mode: far_off / near_off are given, no limit
+  bool arena;                      // arena mode: each leaf's lists are placed where room is
+                                   // reserved for them (far_off / near_off say where)
+  int64_t far_cap, near_cap;       // arena mode: entries the list buffers hold
+  int32_t* temp;                   // arena mode: budget entries per thread of the grid
   int32_t* maxc;                   // [0] longest far list, [1] longest near list
   unsigned long long* stats;       // [0] P2P interactions, [1] float64 decisions, [2] far, [3] near
   int budget;                      // cells one thread visits before handing its leaf on
@@ -81,22 +84,16 @@ __device__ __forceinline__ int open_filter(float4 a, float ha, float4 b, float h
   return -1;
 }
 
-// One thread per leaf.  Slot mode: the lists go to fixed-capacity slots of
-// the leaf (entries beyond the capacity are counted, not stored; the host
-// then grows the slots and walks again, or switches to exact mode).  Exact
-// mode: the counts of a previous pass, scanned, give each leaf's start.
-// A leaf whose walk visits more than W.budget cells (a large leaf in the
-// sparse outskirts of a centrally condensed system opens most of the tree)
-// is queued for k_walk_heavy, which redoes it with a whole block.
-__global__ void __launch_bounds__(128, 10) k_walk(WalkArgs W) {
-  // the grid covers slot_leaves leaves; more leaves than slots is flagged and
-  // the evaluation is redone by the host
-  const int nleaves = W.counters[C_LEAVES];
-  if (!W.exact && nleaves > W.slot_leaves && blockIdx.x == 0 && threadIdx.x == 0)
-    atomicOr(W.status, ST_LISTS);
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nleaves || (!W.exact && k >= W.slot_leaves)) return;
-  {
+// The depth-first walk of leaf k (thread-local).  Far entries go to
+// far[0 ..), near entries to near[0 ..) or, with NEAR_DOWN, to near[0],
+// near[-1], ...; entries beyond a capacity are counted, not stored.  Returns
+// false when the walk passes W.budget visited cells (a large leaf in the
+// sparse outskirts of a centrally condensed system opens most of the tree):
+// the leaf is then queued for k_walk_heavy, which redoes it with a block.
+template <bool NEAR_DOWN>
+__device__ __forceinline__ bool walk_leaf(const WalkArgs& W, int k, int32_t* far, int32_t* near,
+                                          int64_t cap_far, int64_t cap_near, int& nf, int& nn,
+                                          long long& np, int& nex) {
   const int a = W.leaf_cells[k];
   const float4 wa = W.walk[a];
   const float ha = W.walk2[a].x;
@@ -107,28 +104,12 @@ __global__ void __launch_bounds__(128, 10) k_walk(WalkArgs W) {
   const int i_end = W.sys_root[sys + 1];
   const float thf = (float)theta, rkf = (float)W.r_kern;
   const bool always = theta == 0.0;
-  int64_t fo, no;
-  if (W.exact) {
-    fo = W.far_off[k];
-    no = W.near_off[k];
-  } else {
-    fo = (int64_t)k * W.cap_far;
-    no = (int64_t)k * W.cap_near;
-    W.far_off[k] = fo;
-    W.near_off[k] = no;
-  }
-  int32_t* far = W.far_idx + fo;
-  int32_t* near = W.near_idx + no;
-  const int64_t cap_far = W.exact ? INT64_MAX : W.cap_far;
-  const int64_t cap_near = W.exact ? INT64_MAX : W.cap_near;
-  int nf = 0, nn = 0, nex = 0;
-  long long np = 0;
   int i = W.sys_root[sys];              // the walk stays inside the leaf's own tree
   int visits = 0;
   while (i < i_end) {
     if (++visits > W.budget) {
       W.heavy[atomicAdd(W.heavy_n, 1)] = k;
-      return;
+      return false;
     }
     const float4 wb = W.walk[i];
     const float2 w2 = W.walk2[i];
@@ -141,7 +122,7 @@ __global__ void __launch_bounds__(128, 10) k_walk(WalkArgs W) {
     }
     if (o) {
       if (skip == i + 1) {                    // opened leaf: short range
-        if (nn < cap_near) near[nn] = i;
+        if (nn < cap_near) near[NEAR_DOWN ? -nn : nn] = i;
         np += W.count[i];
         ++nn;
       }
@@ -152,15 +133,136 @@ __global__ void __launch_bounds__(128, 10) k_walk(WalkArgs W) {
       i = skip;
     }
   }
-  W.far_cnt[k] = nf;
-  W.near_cnt[k] = nn;
+  return true;
+}
+
+__device__ __forceinline__ void walk_stats(const WalkArgs& W, int k, int nf, int nn, long long np,
+                                           int nex) {
   atomicMax(&W.maxc[0], nf);
   atomicMax(&W.maxc[1], nn);
-  const long long na = W.count[a];
+  const long long na = W.count[W.leaf_cells[k]];
   atomicAdd(&W.stats[0], (unsigned long long)(na * np - na));
+  if (nex) atomicAdd(&W.stats[1], (unsigned long long)nex);
+}
+
+// Slot mode, one thread per leaf: the lists go to fixed-capacity slots of
+// the leaf (entries beyond the capacity are counted, not stored; the host
+// then grows the slots and walks again, or switches to arena mode).
+__global__ void __launch_bounds__(128, 10) k_walk(WalkArgs W) {
+  // the grid covers slot_leaves leaves; more leaves than slots is flagged and
+  // the evaluation is redone by the host
+  const int nleaves = W.counters[C_LEAVES];
+  if (nleaves > W.slot_leaves && blockIdx.x == 0 && threadIdx.x == 0)
+    atomicOr(W.status, ST_LISTS);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nleaves || k >= W.slot_leaves) return;
+  const int64_t fo = (int64_t)k * W.cap_far, no = (int64_t)k * W.cap_near;
+  W.far_off[k] = fo;
+  W.near_off[k] = no;
+  int nf = 0, nn = 0, nex = 0;
+  long long np = 0;
+  if (!walk_leaf<false>(W, k, W.far_idx + fo, W.near_idx + no, W.cap_far, W.cap_near, nf, nn, np,
+                        nex))
+    return;
+  W.far_cnt[k] = nf;
+  W.near_cnt[k] = nn;
   atomicAdd(&W.stats[2], (unsigned long long)nf);
   atomicAdd(&W.stats[3], (unsigned long long)nn);
-  if (nex) atomicAdd(&W.stats[1], (unsigned long long)nex);
+  walk_stats(W, k, nf, nn, np, nex);
+}
+
+// Copies the warp's 32 lists (lane l's list: n entries at src(l), starting at
+// prefix pre[l] of the warp's reserved room dst) with the entries spread
+// evenly over the lanes: entry g belongs to the last list whose prefix is
+// <= g; kCopyBatch independent loads per lane are in flight before storing.
+constexpr int kCopyBatch = 8;
+template <bool DOWN>
+__device__ __forceinline__ void warp_copy(const int32_t* __restrict__ temp, int64_t tid0, int B,
+                                          const int* pre, int total, int32_t* __restrict__ dst) {
+  const int lane = threadIdx.x & 31;
+  for (int g0 = 0; g0 < total; g0 += 32 * kCopyBatch) {
+    int32_t v[kCopyBatch];
+#pragma unroll
+    for (int u = 0; u < kCopyBatch; ++u) {
+      const int g = g0 + 32 * u + lane;
+      v[u] = 0;
+      if (g < total) {
+        int l = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (pre[l + step] <= g) l += step;
+        const int e = g - pre[l];
+        v[u] = temp[(tid0 + l) * B + (DOWN ? B - 1 - e : e)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kCopyBatch; ++u) {
+      const int g = g0 + 32 * u + lane;
+      if (g < total) dst[g] = v[u];
+    }
+  }
+}
+
+// Arena mode (lists of very different lengths, where fixed slots would waste
+// memory): a persistent grid, warp per 32 consecutive leaves, thread per
+// leaf.  Each thread walks into its own scratch of W.budget entries (far
+// from the front, near from the back: a walk within the budget emits at most
+// one entry per visited cell); the warp then reserves room for its 32 leaves'
+// lists with one atomic per list kind on the running totals (stats[2],
+// stats[3]) and copies them there, coalesced.  Totals beyond the buffers
+// flag ST_LISTS and store nothing (counts 0); the host grows and walks again.
+__global__ void __launch_bounds__(128, 10) k_walk_arena(WalkArgs W) {
+  __shared__ int s_pre[4][2][33];         // per warp: exclusive prefixes of the far and near counts
+  const unsigned full = 0xffffffffu;
+  const int nleaves = W.counters[C_LEAVES];
+  const int lane = threadIdx.x & 31;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t tid0 = tid - lane;
+  const int B = W.budget;
+  int32_t* temp = W.temp + tid * B;
+  for (int64_t kb = tid0; kb < nleaves; kb += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)kb + lane;
+    int nf = 0, nn = 0, nex = 0;
+    long long np = 0;
+    bool ok = false;
+    if (k < nleaves)
+      ok = walk_leaf<true>(W, k, temp, temp + (B - 1), INT64_MAX, INT64_MAX, nf, nn, np, nex);
+    if (!ok) nf = nn = 0;
+    int fi = nf, ni = nn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int uf = __shfl_up_sync(full, fi, o), un = __shfl_up_sync(full, ni, o);
+      if (lane >= o) { fi += uf; ni += un; }
+    }
+    const int ftot = __shfl_sync(full, fi, 31), ntot = __shfl_sync(full, ni, 31);
+    unsigned long long fb = 0, nb = 0;
+    if (lane == 0) {
+      fb = atomicAdd(&W.stats[2], (unsigned long long)ftot);
+      nb = atomicAdd(&W.stats[3], (unsigned long long)ntot);
+    }
+    fb = __shfl_sync(full, fb, 0);
+    nb = __shfl_sync(full, nb, 0);
+    const bool fits = (int64_t)(fb + ftot) <= W.far_cap && (int64_t)(nb + ntot) <= W.near_cap;
+    if (!fits && lane == 0) atomicOr(W.status, ST_LISTS);
+    const int64_t myf = (int64_t)fb + fi - nf, myn = (int64_t)nb + ni - nn;
+    if (ok) {
+      W.far_off[k] = myf;
+      W.near_off[k] = myn;
+      W.far_cnt[k] = fits ? nf : 0;
+      W.near_cnt[k] = fits ? nn : 0;
+      walk_stats(W, k, nf, nn, np, nex);
+    }
+    int* pf = s_pre[threadIdx.x >> 5][0];
+    int* pn = s_pre[threadIdx.x >> 5][1];
+    pf[lane] = fi - nf;
+    pn[lane] = ni - nn;
+    if (lane == 31) { pf[32] = fi; pn[32] = ni; }
+    __syncwarp();
+    if (fits) {
+      warp_copy<false>(W.temp, tid0, B, pf, ftot, W.far_idx + fb);
+      warp_copy<true>(W.temp, tid0, B, pn, ntot, W.near_idx + nb);
+    }
+    __syncwarp();
   }
 }
 
@@ -246,14 +348,19 @@ __global__ void __launch_bounds__(kHeavyThreads) k_walk_heavy(WalkArgs W) {
     const int i0 = W.sys_root[sys], i_end = W.sys_root[sys + 1];
     const float thf = (float)theta, rkf = (float)W.r_kern;
     const bool always = theta == 0.0;
-    const int64_t fo = W.exact ? W.far_off[k] : (int64_t)k * W.cap_far;
-    const int64_t no = W.exact ? W.near_off[k] : (int64_t)k * W.cap_near;
-    int32_t* far = W.far_idx + fo;
-    int32_t* near = W.near_idx + no;
-    const int64_t cap_far = W.exact ? INT64_MAX : W.cap_far;
-    const int64_t cap_near = W.exact ? INT64_MAX : W.cap_near;
+    int64_t fo = (int64_t)k * W.cap_far, no = (int64_t)k * W.cap_near;
+    int64_t cap_far = W.cap_far, cap_near = W.cap_near;
+    bool fits = true;
     int nf = 0, nn = 0, carry = 0, nex = 0;
     long long np = 0;
+    // slot mode: one emitting pass; arena mode: a counting pass, then room is
+    // reserved on the running totals and a second pass emits the lists there
+    for (int pass = W.arena ? 0 : 1; pass < 2; ++pass) {
+    const bool emit = pass == 1;
+    int32_t* far = W.far_idx + fo;
+    int32_t* near = W.near_idx + no;
+    nf = nn = carry = nex = 0;
+    np = 0;
     for (int t0 = i0; t0 < i_end;) {
       const int c0 = t0 + kHeavyPer * (int)threadIdx.x;
       int o[kHeavyPer], sk[kHeavyPer];
@@ -297,15 +404,38 @@ __global__ void __launch_bounds__(kHeavyThreads) k_walk_heavy(WalkArgs W) {
       int tf, tn;
       const int2 pos = block_excl_sum2(mf, mn, &tf, &tn, sh_sum);
       int pf = nf + pos.x, pn = nn + pos.y;
+      if (emit) {
 #pragma unroll
-      for (int j = 0; j < kHeavyPer; ++j) {
-        if (ef[j]) { if (pf < cap_far) far[pf] = c0 + j; ++pf; }
-        if (en[j]) { if (pn < cap_near) near[pn] = c0 + j; ++pn; }
+        for (int j = 0; j < kHeavyPer; ++j) {
+          if (ef[j]) { if (pf < cap_far) far[pf] = c0 + j; ++pf; }
+          if (en[j]) { if (pn < cap_near) near[pn] = c0 + j; ++pn; }
+        }
       }
       nf += tf;
       nn += tn;
       carry = max(carry, tile_max);
       t0 = max(t0 + kHeavyTile, carry);
+    }
+    if (!emit) {
+      __shared__ long long sh_base[2];
+      __shared__ int sh_fits;
+      if (threadIdx.x == 0) {
+        const unsigned long long fb = atomicAdd(&W.stats[2], (unsigned long long)nf);
+        const unsigned long long nb = atomicAdd(&W.stats[3], (unsigned long long)nn);
+        const int ok = (int64_t)(fb + nf) <= W.far_cap && (int64_t)(nb + nn) <= W.near_cap;
+        if (!ok) atomicOr(W.status, ST_LISTS);
+        sh_base[0] = (long long)fb;
+        sh_base[1] = (long long)nb;
+        sh_fits = ok;
+      }
+      __syncthreads();
+      fo = sh_base[0];
+      no = sh_base[1];
+      fits = sh_fits != 0;
+      cap_far = cap_near = INT64_MAX;
+      __syncthreads();
+      if (!fits) break;
+    }
     }
     // block sums of the pair count and the float64 decisions
     const unsigned full = 0xffffffffu;
@@ -321,18 +451,18 @@ __global__ void __launch_bounds__(kHeavyThreads) k_walk_heavy(WalkArgs W) {
       long long npt = 0;
       int nxt = 0;
       for (int q2 = 0; q2 < kHeavyWarps; ++q2) { npt += sh_np[q2]; nxt += sh_nex[q2]; }
-      if (!W.exact) {
-        W.far_off[k] = fo;
-        W.near_off[k] = no;
-      }
-      W.far_cnt[k] = nf;
-      W.near_cnt[k] = nn;
+      W.far_off[k] = fo;
+      W.near_off[k] = no;
+      W.far_cnt[k] = fits ? nf : 0;
+      W.near_cnt[k] = fits ? nn : 0;
       atomicMax(&W.maxc[0], nf);
       atomicMax(&W.maxc[1], nn);
       const long long na = W.count[a];
       atomicAdd(&W.stats[0], (unsigned long long)(na * npt - na));
-      atomicAdd(&W.stats[2], (unsigned long long)nf);
-      atomicAdd(&W.stats[3], (unsigned long long)nn);
+      if (!W.arena) {
+        atomicAdd(&W.stats[2], (unsigned long long)nf);
+        atomicAdd(&W.stats[3], (unsigned long long)nn);
+      }
       if (nxt) atomicAdd(&W.stats[1], (unsigned long long)nxt);
     }
     __syncthreads();
@@ -379,13 +509,33 @@ static int ensure_idx(int32_t** idx, int64_t* have, int64_t need, const char* wh
 // Slots waste memory when a few leaves have far longer lists than the rest
 // (small theta on a centrally condensed system): when grown slots would take
 // more than this many bytes and more than twice the bytes of the entries
-// themselves, the lists are stored exactly instead.  The environment variable
-// KDFMM_LIST_MODE=exact forces exact lists (one extra walk pass).
+// themselves, the handle switches to arena mode for good.  The environment
+// variable KDFMM_LIST_MODE=exact starts a handle in arena mode with small
+// buffers (which then grow).
 constexpr int64_t kSlotBudgetBytes = int64_t(1) << 30;
 
-static bool force_exact_lists() {
+static bool force_arena() {
   const char* v = getenv("KDFMM_LIST_MODE");
   return v != nullptr && strcmp(v, "exact") == 0;
+}
+
+// Persistent grid of the arena walk: the resident blocks, at most one thread
+// per leaf.
+static int arena_grid_for(int leaves) {
+  static int per_sm = 0, sms = 0;
+  if (per_sm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_arena, 128, 0) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+      sms = 152;
+    }
+  }
+  return (int)std::max<int64_t>(1, std::min<int64_t>(blocks_for(std::max(leaves, 1), 128),
+                                                     (int64_t)per_sm * sms));
 }
 
 static WalkArgs walk_args(kdfmm_tree_s* t) {
@@ -415,22 +565,56 @@ static WalkArgs walk_args(kdfmm_tree_s* t) {
   return W;
 }
 
-// One walk into the current slots (or exact lists), no synchronisation.
-static void walk_launch(kdfmm_tree_s* t, WalkArgs W, bool exact, int64_t cf, int64_t cn,
+// One walk into the current slots or arena, no synchronisation.
+static void walk_launch(kdfmm_tree_s* t, WalkArgs W, bool arena, int64_t cf, int64_t cn,
                         int slot_leaves, cudaStream_t s) {
   Lists& L = t->L;
-  W.exact = exact;
+  W.arena = arena;
   W.far_idx = L.far_idx;
   W.near_idx = L.near_idx;
   W.cap_far = cf;
   W.cap_near = cn;
+  W.far_cap = L.far_cap;
+  W.near_cap = L.near_cap;
+  W.temp = L.temp;
   W.slot_leaves = slot_leaves;
   cudaMemsetAsync(L.near_np, 0, 4 * sizeof(int64_t), s);
   cudaMemsetAsync(t->counters + C_MAXFAR, 0, 2 * sizeof(int32_t), s);
   cudaMemsetAsync(t->counters + C_HEAVY, 0, sizeof(int32_t), s);
-  k_walk<<<blocks_for(std::max(slot_leaves, 1), 128), 128, 0, s>>>(W);
+  if (arena)
+    k_walk_arena<<<L.arena_grid, 128, 0, s>>>(W);
+  else
+    k_walk<<<blocks_for(std::max(slot_leaves, 1), 128), 128, 0, s>>>(W);
   k_walk_heavy<<<kHeavyGrid, kHeavyThreads, 0, s>>>(W);
   t->launches += 2;
+}
+
+// Scratch of the arena walk over `leaves` leaves (budget entries per thread).
+static int ensure_temp(kdfmm_tree_s* t, int leaves) {
+  Lists& L = t->L;
+  L.arena_grid = arena_grid_for(leaves);
+  const int64_t need = (int64_t)L.arena_grid * 128 * walk_budget();
+  if (L.temp_cap >= need && L.temp != nullptr) return KDFMM_OK;
+  cudaFree(L.temp);
+  L.temp = nullptr;
+  L.temp_cap = 0;
+  if (cudaMalloc(&L.temp, (size_t)need * sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(KDFMM_ERR_OOM, "walk scratch (%lld entries)", (long long)need);
+  }
+  L.temp_cap = need;
+  return KDFMM_OK;
+}
+
+int ensure_arena(kdfmm_tree_s* t, int leaves, double extra) {
+  Lists& L = t->L;
+  const int64_t nf = t->host_stats[KDFMM_STAT_NFAR], nn = t->host_stats[KDFMM_STAT_NNEAR];
+  int rc;
+  if ((rc = ensure_idx(&L.far_idx, &L.far_cap, (int64_t)(nf * extra) + 1024, "far lists", true)))
+    return rc;
+  if ((rc = ensure_idx(&L.near_idx, &L.near_cap, (int64_t)(nn * extra) + 1024, "near lists", true)))
+    return rc;
+  return ensure_temp(t, leaves);
 }
 
 int ensure_slots(kdfmm_tree_s* t, int slot_leaves) {
@@ -445,6 +629,11 @@ int ensure_slots(kdfmm_tree_s* t, int slot_leaves) {
 
 int walk_fixed(kdfmm_tree_s* t, int slot_leaves, cudaStream_t s) {
   Lists& L = t->L;
+  if (L.arena) {
+    if (L.temp == nullptr) return set_error(KDFMM_ERR_INTERNAL, "arena walk scratch not allocated");
+    walk_launch(t, walk_args(t), true, 0, 0, slot_leaves, s);
+    return check_cuda(cudaGetLastError(), "walk launch");
+  }
   if (L.far_cap < (int64_t)slot_leaves * L.cap_far || L.near_cap < (int64_t)slot_leaves * L.cap_near)
     return set_error(KDFMM_ERR_INTERNAL, "list slots not allocated for %d leaves", slot_leaves);
   L.exact = false;
@@ -459,46 +648,53 @@ int run_walk(kdfmm_tree_s* t, cudaStream_t s) {
   WalkArgs W = walk_args(t);
   int32_t* hc = t->host_counters;
   int rc;
-  auto launch = [&](bool exact) {
-    walk_launch(t, W, exact, cf, cn, nl, s);
+  auto launch = [&](bool arena) {
+    walk_launch(t, W, arena, cf, cn, nl, s);
     cudaMemcpyAsync(hc + C_MAXFAR, t->counters + C_MAXFAR, 2 * sizeof(int32_t),
                     cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(t->host_stats + 16, L.near_np, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     return check_cuda(cudaStreamSynchronize(s), "walk");
   };
-  const bool force_exact = force_exact_lists();
+  auto done = [&](bool arena) {
+    L.arena = arena;
+    L.exact = arena;
+    t->host_stats[KDFMM_STAT_NFAR] = t->host_stats[16 + 2];
+    t->host_stats[KDFMM_STAT_NNEAR] = t->host_stats[16 + 3];
+    return check_cuda(cudaGetLastError(), "walk launch");
+  };
+  // arena mode: one pass; a first pass whose lists outgrow the buffers
+  // (counts 0, totals complete) is repeated once with room for the totals
+  auto arena_walk = [&](int64_t want_far, int64_t want_near) {
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      if ((rc = ensure_idx(&L.far_idx, &L.far_cap, want_far, "far lists"))) return rc;
+      if ((rc = ensure_idx(&L.near_idx, &L.near_cap, want_near, "near lists"))) return rc;
+      if ((rc = ensure_temp(t, nl))) return rc;
+      if ((rc = launch(true))) return rc;
+      const int64_t tf = t->host_stats[16 + 2], tn = t->host_stats[16 + 3];
+      if (tf <= L.far_cap && tn <= L.near_cap) return done(true);
+      want_far = tf + tf / 8 + 1024;
+      want_near = tn + tn / 8 + 1024;
+    }
+    return set_error(KDFMM_ERR_CAPACITY, "interaction lists kept outgrowing their buffers");
+  };
+  if (L.arena) return arena_walk(L.far_cap, L.near_cap);
+  if (force_arena()) return arena_walk((int64_t)nl * 64, (int64_t)nl * 16);
   for (int attempt = 0; attempt < 4; ++attempt) {
     if ((rc = ensure_idx(&L.far_idx, &L.far_cap, (int64_t)nl * cf, "far list slots"))) return rc;
     if ((rc = ensure_idx(&L.near_idx, &L.near_cap, (int64_t)nl * cn, "near list slots"))) return rc;
     if ((rc = launch(false))) return rc;
     const int64_t mf = hc[C_MAXFAR], mn = hc[C_MAXNEAR];
     const int64_t tot_far = t->host_stats[16 + 2], tot_near = t->host_stats[16 + 3];
-    if (mf <= cf && mn <= cn && !force_exact) {
+    if (mf <= cf && mn <= cn) {
       L.cap_far = cf;
       L.cap_near = cn;
-      L.exact = false;
-      t->host_stats[KDFMM_STAT_NFAR] = tot_far;
-      t->host_stats[KDFMM_STAT_NNEAR] = tot_near;
-      return check_cuda(cudaGetLastError(), "walk launch");
+      return done(false);
     }
     const int64_t cf2 = std::max<int64_t>(cf, mf + mf / 4 + 16);
     const int64_t cn2 = std::max<int64_t>(cn, mn + mn / 4 + 16);
     const int64_t slot_bytes = (int64_t)nl * (cf2 + cn2) * 4;
-    if (force_exact || (slot_bytes > kSlotBudgetBytes && slot_bytes > 8 * (tot_far + tot_near))) {
-      // exact lists from this pass's counts: one more pass fills them
-      scan_i32_to_i64(L.far_cnt, L.far_off, nl, reinterpret_cast<int64_t*>(t->scan_tmp), s);
-      scan_i32_to_i64(L.near_cnt, L.near_off, nl, reinterpret_cast<int64_t*>(t->scan_tmp), s);
-      t->launches += 6;
-      if ((rc = ensure_idx(&L.far_idx, &L.far_cap, tot_far, "far lists"))) return rc;
-      if ((rc = ensure_idx(&L.near_idx, &L.near_cap, tot_near, "near lists"))) return rc;
-      if ((rc = launch(true))) return rc;
-      if (t->host_stats[16 + 2] != tot_far || t->host_stats[16 + 3] != tot_near)
-        return set_error(KDFMM_ERR_INTERNAL, "the two walk passes disagree");
-      L.exact = true;
-      t->host_stats[KDFMM_STAT_NFAR] = tot_far;
-      t->host_stats[KDFMM_STAT_NNEAR] = tot_near;
-      return check_cuda(cudaGetLastError(), "walk launch");
-    }
+    if (slot_bytes > kSlotBudgetBytes && slot_bytes > 8 * (tot_far + tot_near))
+      return arena_walk(tot_far + tot_far / 8 + 1024, tot_near + tot_near / 8 + 1024);
     cf = cf2;
     cn = cn2;
   }

@@ -147,9 +147,10 @@ def test_batch_of_256_plummer_systems(oracle):
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_exact_lists_match_slots(oracle, monkeypatch, prec):
-    """Exact (compact) interaction lists, the mode taken when a few lists are
-    far longer than the rest, give the same lists and bit-identical forces as
-    fixed slots; the adjoint agrees too."""
+    """Lists placed in reserved room (arena mode, taken when a few lists are
+    far longer than the rest; forced here with buffers too small at first, so
+    the walk also grows them and repeats) give the same lists and
+    bit-identical forces as fixed slots; the adjoint agrees too."""
     import torch
     sizes = [4096, 700, 2500]
     systems = [W.plummer(n, W.seed_for(3, 980 + k)) for k, n in enumerate(sizes)]
@@ -185,15 +186,19 @@ def _batched(f, x, m, off, theta, n_leaf, a, phi):
                              eps=np.full(len(off) - 1, 0.01), n_leaf=n_leaf)
 
 
+@pytest.mark.parametrize("list_mode", ["slots", "arena"])
 @pytest.mark.parametrize("prec", [FP64, MIXED])
-def test_captured_graph_replays_the_eager_evaluation(monkeypatch, prec):
+def test_captured_graph_replays_the_eager_evaluation(monkeypatch, prec, list_mode):
     """Repeated batched calls on the same buffers: the first runs eagerly and
     captures a graph, later ones replay it.  Replays give the eager bits, and
     a replay whose trees outgrow the graph (longer lists after theta drops,
     other system sizes) falls back to the eager path with the same results as
-    a handle that never used a graph."""
+    a handle that never used a graph; with fixed list slots and with lists
+    placed in reserved room (arena mode)."""
     import torch
     from paper_2502_01496_gb300 import native
+    if list_mode == "arena":
+        monkeypatch.setenv("KDFMM_LIST_MODE", "exact")
     systems = [W.plummer(n, W.seed_for(3, 990 + k)) for k, n in enumerate([5000, 3000, 1200, 6000])]
     x0, m0, _, off = _concat(systems)
     n = x0.shape[0]
