@@ -1208,7 +1208,7 @@ __global__ void k_particles32(const Cells c, const int32_t* __restrict__ leaf_ce
                         (float)(tp.z[i] - c.cz[cell]), (float)tp.m[i]);
     const float h = (float)tp.h[i];
     const float hi = h > 0.0f ? 1.0f / h : 0.0f;
-    ph[i] = make_float4(hi, hi * hi * hi, h, 0.0f);
+    ph[i] = make_float4(hi, hi * hi * hi, h, 4.0f * h * h);   // 1/h, 1/h^3, h, (2h)^2
   }
 }
 

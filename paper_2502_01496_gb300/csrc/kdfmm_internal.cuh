@@ -162,7 +162,7 @@ struct kdfmm_tree_s {
   // final tree
   kdfmm::PCols tp{};               // tree order: x y z m h, idx = caller index
   float4* pf = nullptr;            // (x - com_leaf, m) float32
-  float4* ph = nullptr;            // (1/h, 1/h^3, h, 0) float32
+  float4* ph = nullptr;            // (1/h, 1/h^3, h, (2h)^2) float32
   kdfmm::Cells c{};
   int32_t* leaf_cells = nullptr;   // pre-order ids of the leaves
   int32_t* leaf_rank = nullptr;    // cell -> leaf ordinal (-1 for super-cells)

@@ -45,7 +45,7 @@ struct P2PArgs {
   const int64_t* near_off;
   const float4* src32;       // cell (hi, M), (lo, 0), ...
   const float4* pf;          // (x - com_leaf, m)
-  const float4* ph;          // (1/h, 1/h^3, h, 0)
+  const float4* ph;          // (1/h, 1/h^3, h, (2h)^2)
   PCols tp;                  // float64 tree-order particles
   const double* cx;
   const double *cy, *cz;
@@ -252,7 +252,7 @@ __device__ __forceinline__ void newton32(float rx, float ry, float rz, float mj,
 __device__ __forceinline__ void newton32_outside(float rx, float ry, float rz, float r2, float mj,
                                                  bool inside, float& fx, float& fy, float& fz,
                                                  float& fp) {
-  const float inv = rsqrtf(r2);
+  const float inv = rsqrtf(r2);                 // infinite for coincident pairs: selected away
   const float m1 = mj * inv;
   const float minv = inside ? 0.0f : m1;
   const float f = inside ? 0.0f : m1 * inv * inv;
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
         // which are marked in a bit mask instead; pass 2 visits only the
         // marked pairs with the full symmetrised M4 pair.  Only a sixth of the
         // segment's pairs is inside, and a lane's marked pairs are dense work.
-        const float h2i = 4.0f * hi.z * hi.z;
+        const float h2i = hi.w;                                   // (2 h_i)^2
         const int j0 = kStageCap - nK + sl;
         const int npair = j0 < kStageCap ? (kStageCap - j0 + K - 1) / K : 0;
         for (int i0 = 0; i0 < npair; i0 += 128) {
@@ -423,10 +423,9 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
             for (int b = 0; b < nbw; ++b) {
               const int j = jb + K * (32 * w + b);
               const float4 s = sp[j];
-              const float hj = sk[j].z;
               const float rx = xa.x - s.x, ry = xa.y - s.y, rz = xa.z - s.z;
               const float r2 = rx * rx + ry * ry + rz * rz;
-              const bool inside = r2 < fmaxf(h2i, 4.0f * hj * hj);
+              const bool inside = r2 < fmaxf(h2i, sk[j].w);        // inside (2 max(h_i, h_j))
               in[w] |= (uint32_t)inside << b;
               newton32_outside(rx, ry, rz, r2, s.w, inside, fx, fy, fz, fp);
             }

@@ -145,12 +145,15 @@ def test_batch_of_256_plummer_systems(oracle):
         assert ea.max() < 2e-5 and ep.max() < 2e-5, (k, ea.max(), ep.max())
 
 
+@pytest.mark.parametrize("mode", ["exact", "two_pass"])
 @pytest.mark.parametrize("prec", [FP64, MIXED])
-def test_exact_lists_match_slots(oracle, monkeypatch, prec):
+def test_exact_lists_match_slots(oracle, monkeypatch, prec, mode):
     """Lists placed in reserved room (arena mode, taken when a few lists are
     far longer than the rest; forced here with buffers too small at first, so
-    the walk also grows them and repeats) give the same lists and
-    bit-identical forces as fixed slots; the adjoint agrees too."""
+    the walk also grows them and repeats) and two-pass lists (count, scan,
+    fill: the fallback when the arena walk's scratch cannot be allocated) give
+    the same lists and bit-identical forces as fixed slots; the adjoint agrees
+    too."""
     import torch
     sizes = [4096, 700, 2500]
     systems = [W.plummer(n, W.seed_for(3, 980 + k)) for k, n in enumerate(sizes)]
@@ -162,7 +165,7 @@ def test_exact_lists_match_slots(oracle, monkeypatch, prec):
     rng = np.random.default_rng(3)
     ab = _cuda(rng.standard_normal((off[-1], 3)))
     xb1, mb1 = f1.vjp(ab)
-    monkeypatch.setenv("KDFMM_LIST_MODE", "exact")
+    monkeypatch.setenv("KDFMM_LIST_MODE", mode)
     f2, _, ga2, gp2 = _run_forest(systems, theta, eps, n_leaf, prec, 0)
     ex2 = f2.export(lists=True)
     xb2, mb2 = f2.vjp(ab)

@@ -37,13 +37,13 @@ def _eval(ps, theta, prec, n_leaf=16):
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])
 @pytest.mark.parametrize("budget", ["1", "37"])
-@pytest.mark.parametrize("list_mode", ["slots", "exact"])
+@pytest.mark.parametrize("list_mode", ["slots", "exact", "two_pass"])
 def test_block_walk_equals_thread_walk(oracle, monkeypatch, prec, budget, list_mode):
     """A budget of 1 hands every leaf to the block-wide walk, 37 about half
     of them: lists, statistics and force bits equal the thread walk's."""
     ps = W.plummer(4096, W.seed_for(0, 96))
-    if list_mode == "exact":
-        monkeypatch.setenv("KDFMM_LIST_MODE", "exact")
+    if list_mode != "slots":
+        monkeypatch.setenv("KDFMM_LIST_MODE", list_mode)
     f0, a0, p0 = _eval(ps, 0.5, prec)
     ex0, st0 = f0.export(lists=True), f0.stats()
     monkeypatch.setenv("KDFMM_WALK_BUDGET", budget)
