@@ -58,6 +58,8 @@ def parse():
                     help="steps of the 256-system batch (0 skips it)")
     ap.add_argument("--variant-steps", type=int, default=5,
                     help="steps of the dual-walk and standard-expansion variants (0 skips them)")
+    ap.add_argument("--large-steps", type=int, default=3,
+                    help="steps of the 2^24-particle uniform + clumps evaluation (0 skips it)")
     return ap.parse_args()
 
 
@@ -313,6 +315,57 @@ def run_batched(args, dev, flush):
     return out
 
 
+def run_large(args, dev, flush):
+    """The large single evaluation: 2^24 particles, half uniform in the unit
+    cube and half in 64 Gaussian clumps (sigma 0.01), masses log-uniform over a
+    decade, eps 1e-3, theta 0.5, leaves of at most 32, mixed precision; the
+    same step as the headline (build + evaluation + total momentum)."""
+    import statistics
+    import torch
+    from paper_2502_01496_gb300 import native
+    from paper_2502_01496_gb300 import workloads as W
+    ps = W.uniform_clumps(1 << 24, W.seed_for(2))
+    n = ps.n
+    x = torch.tensor(ps.x, device=dev)
+    m = torch.tensor(ps.m, device=dev)
+    a = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    F = torch.empty(3, dtype=torch.float64, device=dev)
+    f = native.KdFmm(theta=0.5, eps=ps.eps, n_leaf=32, soft_kind=0, precision=native.MIXED)
+
+    def step():
+        f.build(x, m)
+        f.accel(a, phi)
+        native.total_momentum(m, a, F)
+
+    for _ in range(2):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    native.tree_timing(f.handle, True, read=False)
+    ts, phases = [], []
+    for _ in range(args.large_steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        phases.append(native.tree_timing(f.handle, True))
+    native.tree_timing(f.handle, False, read=False)
+    st = f.stats()
+    ms = statistics.mean(ts)
+    out = {"workload": "uniform_clumps_16777216", "n": n, "theta": 0.5, "n_leaf": 32,
+           "precision": "mixed", "unit": UNIT, "value": n / (ms / 1e3) / 1e6, "ms_per_step": ms,
+           "steps": args.large_steps,
+           "phases_ms": {k: statistics.mean(p[k] for p in phases) for k in phases[0]},
+           "p2p": st["np2p"], "m2l": st["nfar"], "nleaves": st["nleaves"], "ncells": st["ncells"]}
+    del f, x, m, a, phi
+    return out
+
+
 def run_variants(args, ps, x, m, h, flush):
     """The same workload under the method's variants: the paper's leaf-only walk
     with Eq. 6 (the headline), the symmetric dual-tree walk, and the standard
@@ -511,6 +564,9 @@ def run_ours(args):
     variants = None
     if args.variant_steps > 0:
         variants = run_variants(args, ps, x, m, h, flush)
+    large = None
+    if args.large_steps > 0 and rank == 0 and world == 1:
+        large = run_large(args, dev, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -530,6 +586,7 @@ def run_ours(args):
             "phases_ms": phase_mean,
             "batched": batched,
             "variants": variants,
+            "large": large,
             "interactions": {"p2p": st["np2p"], "m2l": st["nfar"], "nleaves": st["nleaves"],
                              "ncells": st["ncells"], "p2p_per_s": st["np2p"] / (ms_per_step / 1e3),
                              "m2l_per_s": st["nfar"] / (ms_per_step / 1e3)},
