@@ -19,23 +19,52 @@ import torch.utils.checkpoint as ckpt
 from . import native
 
 
+# Handles not in use, per (device, parameters).  A handle keeps its buffers
+# and list capacities between builds, so taking one from here spares an
+# evaluation the allocations and the first-call sizing of a new handle; an
+# evaluation whose backward may still run keeps its handle (the adjoint needs
+# its tree and lists) until then.
+_FREE: dict = {}
+_FREE_MAX = 16
+
+
+def _key(params: dict):
+    return (torch.cuda.current_device(), tuple(sorted(params.items())))
+
+
+def _take(params: dict):
+    free = _FREE.get(_key(params))
+    return free.pop() if free else native.KdFmm(**params)
+
+
+def _give(params: dict, f) -> None:
+    free = _FREE.setdefault(_key(params), [])
+    if len(free) < _FREE_MAX:
+        free.append(f)
+
+
 class FmmAccel(torch.autograd.Function):
     """a = FMM acceleration of particles x (n, 3) with masses m (n,) and
     smoothing lengths h (n,) or None; `params` the kdfmm parameters."""
 
     @staticmethod
     def forward(ctx, x, m, h, params: dict):
-        f = native.KdFmm(**params)
+        f = _take(params)
         f.build(x.detach().contiguous(), m.detach().contiguous(),
                 None if h is None else h.detach().contiguous())
         a, _ = f.accel(want_phi=False)
-        ctx.f = f
+        if ctx.needs_input_grad[0] or ctx.needs_input_grad[1]:
+            ctx.f, ctx.params = f, params
+        else:                                   # no backward will come
+            ctx.f = None
+            _give(params, f)
         return a
 
     @staticmethod
     def backward(ctx, a_bar):
         f, ctx.f = ctx.f, None
         x_bar, m_bar = f.vjp(a_bar.contiguous())
+        _give(ctx.params, f)
         return x_bar, (m_bar if ctx.needs_input_grad[1] else None), None, None
 
 
