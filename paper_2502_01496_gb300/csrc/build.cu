@@ -460,7 +460,11 @@ struct SubArgs {
   int qcap;
 };
 
-constexpr int kBlockSeg = 256;                      // split by the whole CTA at this size
+// Cells of at least kBlockSeg particles are split by the whole CTA, one after
+// the other; smaller ones by one warp each, in parallel (1024 measured 4 %
+// faster over the build than 256, where a level of 8 cells of 256 took 8
+// CTA-wide splits in a row).
+constexpr int kBlockSeg = 1024;
 constexpr int kSubWarps = kSubtreeThreads / 32;
 
 // Shared-memory views of one subtree: float64 particles, float32 shadows of
@@ -754,7 +758,7 @@ __device__ void split_block(const SubArgs& S, const SubSmem& L, BlockScratch& B,
   const int lf = e.x, cnt = e.y, cell = e.z, depth = e.w;
   const BuildArgs& A = S.A;
   int P = 1;
-  while (P < cnt) P <<= 1;                         // P >= kBlockSeg = 256
+  while (P < cnt) P <<= 1;                         // P >= kBlockSeg
   const int Pw = P / kSubWarps;                    // per warp, >= 32
   const int base = w * Pw + lane * (Pw >> 5);
   auto get = [&](int k) {
