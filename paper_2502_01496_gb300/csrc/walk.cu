@@ -86,16 +86,14 @@ __device__ __forceinline__ int open_filter(float4 a, float ha, float4 b, float h
   return -1;
 }
 
-// The depth-first walk of leaf k (thread-local).  Far entries go to
-// far[0 ..), near entries to near[0 ..) or, with NEAR_DOWN, to near[0],
-// near[-1], ...; entries beyond a capacity are counted, not stored.  Returns
-// false when the walk passes W.budget visited cells (a large leaf in the
-// sparse outskirts of a centrally condensed system opens most of the tree):
-// the leaf is then queued for k_walk_heavy, which redoes it with a block.
-template <bool NEAR_DOWN>
+// The depth-first walk of leaf k into one thread's arena scratch: far entries
+// to far[0 ..), near entries to near[0], near[-1], ... (the scratch's other
+// end).  Returns false when the walk passes W.budget visited cells (a large
+// leaf in the sparse outskirts of a centrally condensed system opens most of
+// the tree): the leaf is then queued for k_walk_heavy, which redoes it with a
+// block.
 __device__ __forceinline__ bool walk_leaf(const WalkArgs& W, int k, int32_t* far, int32_t* near,
-                                          int64_t cap_far, int64_t cap_near, int& nf, int& nn,
-                                          long long& np, int& nex) {
+                                          int& nf, int& nn, long long& np, int& nex) {
   const int a = W.leaf_cells[k];
   const float4 wa = W.walk[a];
   const float ha = W.walk2[a].x;
@@ -124,13 +122,13 @@ __device__ __forceinline__ bool walk_leaf(const WalkArgs& W, int k, int32_t* far
     }
     if (o) {
       if (skip == i + 1) {                    // opened leaf: short range
-        if (nn < cap_near) near[NEAR_DOWN ? -nn : nn] = i;
+        near[-nn] = i;
         np += W.count[i];
         ++nn;
       }
       i = i + 1;
     } else {                                  // closed: long range, skip its subtree
-      if (nf < cap_far) far[nf] = i;
+      far[nf] = i;
       ++nf;
       i = skip;
     }
@@ -152,8 +150,9 @@ __device__ __forceinline__ void walk_stats(const WalkArgs& W, int k, int nf, int
 // then grows the slots and walks again, or changes mode).  Two-pass mode: the
 // counts of a previous pass, scanned, give each leaf's start.  A leaf whose
 // walk passes W.budget visited cells is queued for k_walk_heavy.  (The walk
-// is written out here rather than through walk_leaf: this form measured 7 %
-// faster on the slot-mode benchmark walk.)
+// is written out here, with the offsets either computed or given, rather than
+// shared with walk_leaf: this form measured 7 % faster in ncu kernel time on
+// the slot-mode benchmark walk.)
 __global__ void __launch_bounds__(128, 10) k_walk(WalkArgs W) {
   // the grid covers slot_leaves leaves; more leaves than slots is flagged and
   // the evaluation is redone by the host
@@ -285,7 +284,7 @@ __global__ void __launch_bounds__(128, 10) k_walk_arena(WalkArgs W) {
     long long np = 0;
     bool ok = false;
     if (k < nleaves)
-      ok = walk_leaf<true>(W, k, temp, temp + (B - 1), INT64_MAX, INT64_MAX, nf, nn, np, nex);
+      ok = walk_leaf(W, k, temp, temp + (B - 1), nf, nn, np, nex);
     if (!ok) nf = nn = 0;
     int fi = nf, ni = nn;
 #pragma unroll
