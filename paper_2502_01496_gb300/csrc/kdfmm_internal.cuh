@@ -204,6 +204,8 @@ struct kdfmm_tree_s {
     int32_t* cursor = nullptr;           // per cell (fill cursors)
     float* lcell32 = nullptr;            // 24 per cell
     double* lcell64 = nullptr;           // 20 per cell
+    double* ltot = nullptr;              // 20 per cell: own + ancestors' expansions, at its com
+    int64_t ltot_cap = 0;
     int64_t nfar = 0, nnear = 0;         // entries (both directions)
   } dual;
 
