@@ -177,7 +177,13 @@ int kdfmm_tree_moments(kdfmm_tree t, const double* x, const double* m, const dou
  * M2L (Eq. 6), L2P (Eq. 8), softened P2P (Eq. 13 / Plummer), a = a_short +
  * a_long (Eq. 3).  a: N x 3 output, phi: N output potential or NULL (the
  * potential is the third-order expansion of -M/R - Q_jk R_j R_k/(2R^5) plus
- * the softened pair potentials).  Synchronises `stream` once (list sizes). */
+ * the softened pair potentials).  The handle keeps the interaction lists in
+ * fixed slots per leaf or, when a few lists are far longer than the rest (a
+ * centrally condensed system), in room reserved per leaf by a one-pass walk
+ * whose threads each use a scratch of 4096 int32 entries (at most ~3.2 GB;
+ * when that cannot be allocated, in two passes: count, then fill).
+ * Synchronises `stream` once (list sizes), again when the lists outgrew their
+ * buffers and the walk is repeated. */
 int kdfmm_fmm_accel(kdfmm_tree t, double* a, double* phi, void* stream);
 
 /* Vector-Jacobian product of the last evaluation's accelerations with respect
