@@ -278,6 +278,10 @@ __global__ void __launch_bounds__(128, 10) k_walk_arena(WalkArgs W) {
   const int64_t tid0 = tid - lane;
   const int B = W.budget;
   int32_t* temp = W.temp + tid * B;
+  // one round (every leaf has a thread): leaf k's scratch is thread k's and
+  // k_arena_copy moves the lists afterwards, with all of the GPU's loads in
+  // flight at once; with more rounds each warp copies before its next round
+  const bool deferred = (int64_t)gridDim.x * blockDim.x >= nleaves;
   for (int64_t kb = tid0; kb < nleaves; kb += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)kb + lane;
     int nf = 0, nn = 0, nex = 0;
@@ -309,6 +313,9 @@ __global__ void __launch_bounds__(128, 10) k_walk_arena(WalkArgs W) {
       W.far_cnt[k] = fits ? nf : 0;
       W.near_cnt[k] = fits ? nn : 0;
       walk_stats(W, k, nf, nn, np, nex);
+    } else if (k < nleaves) {         // queued: k_walk_heavy writes its lists and counts
+      W.far_cnt[k] = 0;
+      W.near_cnt[k] = 0;
     }
     int* pf = s_pre[threadIdx.x >> 5][0];
     int* pn = s_pre[threadIdx.x >> 5][1];
@@ -316,11 +323,30 @@ __global__ void __launch_bounds__(128, 10) k_walk_arena(WalkArgs W) {
     pn[lane] = ni - nn;
     if (lane == 31) { pf[32] = fi; pn[32] = ni; }
     __syncwarp();
-    if (fits) {
+    if (fits && !deferred) {
       warp_copy<false>(W.temp, tid0, B, pf, ftot, W.far_idx + fb);
       warp_copy<true>(W.temp, tid0, B, pn, ntot, W.near_idx + nb);
     }
     __syncwarp();
+  }
+}
+
+// The deferred copy of a one-round arena walk (k_walk_arena's `deferred`):
+// warp per leaf, lanes over its entries; leaf k's lists are in the scratch of
+// thread k.  Runs before k_walk_heavy, while the queued leaves' counts are 0.
+__global__ void k_arena_copy(WalkArgs W, int64_t walk_threads) {
+  const int nleaves = W.counters[C_LEAVES];
+  if (nleaves > walk_threads) return;            // the walk copied its lists itself
+  const int lane = threadIdx.x & 31;
+  const int B = W.budget;
+  for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < nleaves;
+       k += (int)((gridDim.x * blockDim.x) >> 5)) {
+    const int32_t* src = W.temp + (int64_t)k * B;
+    const int nf = W.far_cnt[k], nn = W.near_cnt[k];
+    int32_t* far = W.far_idx + W.far_off[k];
+    int32_t* near = W.near_idx + W.near_off[k];
+    for (int e = lane; e < nf; e += 32) far[e] = src[e];
+    for (int e = lane; e < nn; e += 32) near[e] = src[B - 1 - e];
   }
 }
 
@@ -647,10 +673,13 @@ static void walk_launch(kdfmm_tree_s* t, WalkArgs W, ListMode mode, int64_t cf, 
   cudaMemsetAsync(L.near_np, 0, 4 * sizeof(int64_t), s);
   cudaMemsetAsync(t->counters + C_MAXFAR, 0, 2 * sizeof(int32_t), s);
   cudaMemsetAsync(t->counters + C_HEAVY, 0, sizeof(int32_t), s);
-  if (arena)
+  if (arena) {
     k_walk_arena<<<L.arena_grid, 128, 0, s>>>(W);
-  else
+    k_arena_copy<<<kGridBlocks, 256, 0, s>>>(W, (int64_t)L.arena_grid * 128);
+    t->launches += 1;
+  } else {
     k_walk<<<blocks_for(std::max(slot_leaves, 1), 128), 128, 0, s>>>(W);
+  }
   k_walk_heavy<<<kHeavyGrid, kHeavyThreads, 0, s>>>(W);
   t->launches += 2;
 }
