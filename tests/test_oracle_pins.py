@@ -462,3 +462,126 @@ def test_m4_pair_is_symmetric_and_newtonian_outside_support(oracle):
         if r >= 2 * max(hi, hj):
             np.testing.assert_allclose(ai, -mj * d / r ** 3, rtol=1e-13)
             assert pi == pytest.approx(-mj / r, rel=1e-13)
+
+
+# --------------------------------------------------------------------------
+# frozen topology (reading: same cells and particle order, new x, m, h) and
+# evaluation from given lists
+# --------------------------------------------------------------------------
+
+def _frozen_definitions(c, order, x, m, h):
+    """Per-cell M, centre of mass, s, h_max and traceless Q (Sec. 2, Eq. 7)
+    written out from the particles of each cell's range [first, first+count)."""
+    out = []
+    for k in range(len(c.first)):
+        idx = order[c.first[k]:c.first[k] + c.count[k]]
+        xs, ms = x[idx], m[idx]
+        M = math.fsum(ms)
+        com = np.array([math.fsum(ms * xs[:, d]) for d in range(3)]) / M
+        y = xs - com
+        s = np.sqrt((y * y).sum(1)).max()
+        Qf = 3 * np.einsum("n,ni,nj->ij", ms, y, y) - np.eye(3) * np.sum(ms * (y * y).sum(1))
+        out.append((M, com, s, h[idx].max(), Qf[[0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]]))
+    return out
+
+
+@pytest.mark.parametrize("kind", ["polytrope_m4", "plummer"])
+def test_moments_frozen_against_definitions(oracle, kind):
+    """After moving every particle, changing every mass and smoothing length,
+    the frozen-topology moments of each cell equal the definitions over the
+    cell's unchanged particle range: M and centre of mass (Sec. 2), s = the
+    largest distance from the new centre of mass, h_max, and Q (Eq. 7) about
+    the new centre of mass.  A super-cell's M is exactly its children's sum.
+    At unchanged inputs a leaf's moments equal the fresh build's bit for bit
+    (both are the same pairwise sums over the leaf in caller order)."""
+    if kind == "polytrope_m4":
+        ps = W.polytrope_binary(700, W.seed_for(1, 7))
+        T = oracle.Tree(ps.x, ps.m, ps.h, theta=0.5, n_leaf=10, soft_kind=oracle.SOFT_M4, eps=ps.eps)
+    else:
+        ps = W.plummer(2000, W.seed_for(0, 7))
+        T = oracle.Tree(ps.x, ps.m, theta=0.5, n_leaf=16, eps=ps.eps)
+    c0 = T.cells()
+    order = T.order()
+    leaf = c0.left < 0
+
+    T.moments_frozen(ps.x, ps.m, ps.h)
+    c1 = T.cells()
+    for f in ("M", "com", "s", "hmax"):
+        assert np.array_equal(getattr(c1, f)[leaf], getattr(c0, f)[leaf]), f
+    np.testing.assert_allclose(c1.M, c0.M, rtol=1e-14)
+    np.testing.assert_allclose(c1.com, c0.com, rtol=1e-13, atol=1e-15)
+
+    rng = np.random.default_rng(77)
+    x1 = ps.x + rng.normal(0.0, 0.02, ps.x.shape)
+    m1 = ps.m * rng.uniform(0.5, 2.0, ps.n)
+    h1 = None if ps.h is None else ps.h * rng.uniform(0.8, 1.25, ps.n)
+    T.moments_frozen(x1, m1, h1)
+    c2 = T.cells()
+    for f in ("first", "count", "left", "right", "parent", "skip", "depth"):
+        assert np.array_equal(getattr(c2, f), getattr(c0, f)), f
+    assert np.array_equal(T.order(), order)
+    hh = np.full(ps.n, ps.eps) if h1 is None else h1
+    ref = _frozen_definitions(c2, order, x1, m1, hh)
+    for k, (M, com, s, hmax, Q) in enumerate(ref):
+        assert c2.M[k] == pytest.approx(M, rel=1e-13)
+        np.testing.assert_allclose(c2.com[k], com, rtol=1e-12, atol=1e-14)
+        assert c2.s[k] == pytest.approx(s, rel=1e-12)
+        assert c2.hmax[k] == hmax
+        np.testing.assert_allclose(c2.Q[k], Q, atol=1e-12 * max(1e-300, c2.M[k] * c2.s[k] ** 2))
+        if c2.left[k] >= 0:
+            assert c2.M[k] == c2.M[c2.left[k]] + c2.M[c2.right[k]]
+    # the moved moments differ from the original ones (the call is not a no-op)
+    assert not np.array_equal(c2.com, c0.com)
+
+
+def test_eval_lists_reproduces_eval_and_reads_its_lists(oracle):
+    """Evaluation from given lists: with the walk's own lists it is the
+    evaluation bit for bit (Sec. 4's leaf walk feeds Eq. 3); with every leaf
+    listing every leaf as near and nothing far it is the O(N^2) direct sum;
+    and the order in which leaves are listed does not matter."""
+    ps = W.polytrope_binary(600, W.seed_for(1, 8))
+    T = oracle.Tree(ps.x, ps.m, ps.h, theta=0.5, n_leaf=12, soft_kind=oracle.SOFT_M4, eps=ps.eps)
+    a0, p0 = T.eval()
+    L = T.walk()
+    assert len(L.far_idx) > 0 and len(L.near_idx) > 0
+    a1, p1 = T.eval_lists(L)
+    assert np.array_equal(a1, a0) and np.array_equal(p1, p0)
+
+    # leaves listed in reverse, each with its own lists
+    nl = len(L.leaf_ids)
+    rev = np.arange(nl)[::-1]
+    fo = np.concatenate([[0], np.cumsum(np.diff(L.far_off)[rev])])
+    no = np.concatenate([[0], np.cumsum(np.diff(L.near_off)[rev])])
+    fi = np.concatenate([L.far_idx[L.far_off[k]:L.far_off[k + 1]] for k in rev])
+    ni = np.concatenate([L.near_idx[L.near_off[k]:L.near_off[k + 1]] for k in rev])
+    Lr = oracle.Lists(L.leaf_ids[rev].copy(), fo, fi.astype(np.int32), no, ni.astype(np.int32), 0)
+    a2, p2 = T.eval_lists(Lr)
+    assert np.array_equal(a2, a0) and np.array_equal(p2, p0)
+
+    # all near, nothing far: the direct sum (j != i, same pair interaction)
+    leaves = L.leaf_ids.astype(np.int32)
+    Ld = oracle.Lists(leaves, np.zeros(nl + 1, dtype=np.int64), np.zeros(0, dtype=np.int32),
+                      np.arange(nl + 1, dtype=np.int64) * nl, np.tile(leaves, nl), 0)
+    a3, p3 = T.eval_lists(Ld)
+    ad, pd = oracle.direct(ps.x, ps.m, ps.h, soft_kind=oracle.SOFT_M4, eps=ps.eps)
+    assert np.max(rel_err(a3, ad)) < 1e-13
+    np.testing.assert_allclose(p3, pd, rtol=1e-13)
+
+
+def test_frozen_lists_on_moved_particles_at_theta_zero_are_direct(oracle):
+    """theta = 0 opens every cell (Sec. 2), so the frozen lists are all near;
+    after moving the particles and changing their masses, the evaluation
+    from those lists on the frozen-topology moments is the direct sum of the
+    moved system."""
+    ps = W.plummer(900, W.seed_for(0, 9))
+    T = oracle.Tree(ps.x, ps.m, theta=0.0, n_leaf=16, eps=ps.eps)
+    L = T.walk()
+    assert len(L.far_idx) == 0
+    rng = np.random.default_rng(5)
+    x1 = ps.x + rng.normal(0.0, 0.05, ps.x.shape)
+    m1 = ps.m * rng.uniform(0.5, 2.0, ps.n)
+    T.moments_frozen(x1, m1, None)
+    a, p = T.eval_lists(L)
+    ad, pd = oracle.direct(x1, m1, eps=ps.eps)
+    assert np.max(rel_err(a, ad)) < 1e-13
+    np.testing.assert_allclose(p, pd, rtol=1e-13)
