@@ -78,12 +78,22 @@ __device__ __forceinline__ float m4_pot(float q, float qi) {
 }
 __device__ __forceinline__ double m4_fq3_d(double q, double qi) {
   if (q < 1.0) return 4.0 / 3.0 + q * q * (-1.2 + 0.5 * q);
-  return 8.0 / 3.0 + q * (-3.0 + q * (1.2 - q / 6.0)) - qi * qi * qi / 15.0;
+  return 8.0 / 3.0 + q * (-3.0 + q * (1.2 - q * (1.0 / 6.0))) - qi * qi * qi * (1.0 / 15.0);
 }
 __device__ __forceinline__ double m4_pot_d(double q, double qi) {
   const double q2 = q * q;
   if (q < 1.0) return 1.4 + q2 * (-2.0 / 3.0 + q2 * (0.3 - 0.1 * q));
-  return 1.6 + q2 * (-4.0 / 3.0 + q * (1.0 + q * (-0.3 + q / 30.0))) - qi / 15.0;
+  return 1.6 + q2 * (-4.0 / 3.0 + q * (1.0 + q * (-0.3 + q * (1.0 / 30.0)))) - qi * (1.0 / 15.0);
+}
+
+// Reciprocal square root, flush-to-zero form of the hardware approximation
+// (relative error below 2^-22).  Its arguments here are 0 (coincident
+// particles, selected away) or far above the subnormal range, where the
+// flush changes nothing and the subnormal fix-up of rsqrtf is dead weight.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // Interaction of one target with one source, float32, accumulated into f*.
@@ -93,14 +103,14 @@ __device__ __forceinline__ void pair32(float rx, float ry, float rz, float mj, c
                                        float& fz, float& fp) {
   if (SOFT == KDFMM_SOFT_PLUMMER) {
     const float r2 = rx * rx + ry * ry + rz * rz + eps2;
-    const float inv = rsqrtf(r2);
+    const float inv = rsqrt_ftz(r2);
     const float minv = mj * inv;
     const float f = minv * inv * inv;
     fx -= f * rx; fy -= f * ry; fz -= f * rz;
     fp -= minv;
   } else {
     const float r2 = fmaxf(rx * rx + ry * ry + rz * rz, 1e-30f);
-    const float inv = rsqrtf(r2);
+    const float inv = rsqrt_ftz(r2);
     const float r = r2 * inv;
     const float qa = r * hi.x, qb = r * hj.x;
     float f, p;
@@ -153,7 +163,7 @@ __device__ __forceinline__ void m4pair32(float rx, float ry, float rz, float mj,
                                          const float4& hj, float& fx, float& fy, float& fz,
                                          float& fp) {
   const float r2 = fmaxf(rx * rx + ry * ry + rz * rz, 1e-30f);
-  const float inv = rsqrtf(r2);
+  const float inv = rsqrt_ftz(r2);
   const float r = r2 * inv;
   const float inv3 = inv * inv * inv;
   float fa, pa, fb, pb;
@@ -162,45 +172,6 @@ __device__ __forceinline__ void m4pair32(float rx, float ry, float rz, float mj,
   const float mf = 0.5f * mj * (fa + fb);
   fx -= mf * rx; fy -= mf * ry; fz -= mf * rz;
   fp -= 0.5f * mj * (pa + pb);
-}
-
-template <int SOFT>
-__device__ __forceinline__ void pair64(double rx, double ry, double rz, double mj, double hi,
-                                       double hj, double eps2, double& fx, double& fy, double& fz,
-                                       double& fp) {
-  if (SOFT == KDFMM_SOFT_PLUMMER) {
-    const double r2 = rx * rx + ry * ry + rz * rz + eps2;
-    const double inv = 1.0 / sqrt(r2);
-    const double minv = mj * inv;
-    const double f = minv * inv * inv;
-    fx -= f * rx; fy -= f * ry; fz -= f * rz;
-    fp -= minv;
-  } else {
-    const double r2 = rx * rx + ry * ry + rz * rz;
-    if (r2 == 0.0) {
-      fp -= mj * 0.5 * (1.4 / hi + 1.4 / hj);
-      return;
-    }
-    const double r = sqrt(r2);
-    const double inv = 1.0 / r;
-    const double qa = r / hi, qb = r / hj;
-    double f, p;
-    if (qa < 2.0 || qb < 2.0) {
-      const double inv3 = inv * inv * inv;
-      const double fa = qa < 2.0 ? m4_fq3_d(qa, hi * inv) / (hi * hi * hi) : inv3;
-      const double fb = qb < 2.0 ? m4_fq3_d(qb, hj * inv) / (hj * hj * hj) : inv3;
-      const double pa = qa < 2.0 ? m4_pot_d(qa, hi * inv) / hi : inv;
-      const double pb = qb < 2.0 ? m4_pot_d(qb, hj * inv) / hj : inv;
-      f = 0.5 * (fa + fb);
-      p = 0.5 * (pa + pb);
-    } else {
-      f = inv * inv * inv;
-      p = inv;
-    }
-    const double mf = mj * f;
-    fx -= mf * rx; fy -= mf * ry; fz -= mf * rz;
-    fp -= mj * p;
-  }
 }
 
 // L2P of the 20 coefficients at x: a = -(C1 + C2 x + C3 x x / 2),
@@ -240,7 +211,7 @@ __device__ __forceinline__ void near_leaf32(const P2PArgs& A, int fb, int nb, in
 __device__ __forceinline__ void newton32(float rx, float ry, float rz, float mj, float eps2,
                                          float& fx, float& fy, float& fz, float& fp) {
   const float r2 = rx * rx + ry * ry + rz * rz + eps2;
-  const float inv = rsqrtf(r2);
+  const float inv = rsqrt_ftz(r2);
   const float minv = mj * inv;
   const float f = minv * inv * inv;
   fx -= f * rx; fy -= f * ry; fz -= f * rz;
@@ -252,7 +223,7 @@ __device__ __forceinline__ void newton32(float rx, float ry, float rz, float mj,
 __device__ __forceinline__ void newton32_outside(float rx, float ry, float rz, float r2, float mj,
                                                  bool inside, float& fx, float& fy, float& fz,
                                                  float& fp) {
-  const float inv = rsqrtf(r2);                 // infinite for coincident pairs: selected away
+  const float inv = rsqrt_ftz(r2);              // infinite for coincident pairs: selected away
   const float m1 = mj * inv;
   const float minv = inside ? 0.0f : m1;
   const float f = inside ? 0.0f : m1 * inv * inv;
@@ -485,13 +456,76 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
   }
 }
 
+constexpr int kStage64 = 128;      // staged sources per warp and chunk (float64 path)
+constexpr int kP2P64Warps = 4;
+
+// Float64 pair on target i from source j, d = x_i - x_j; hinv = 1/h and
+// hinv3 = 1/h^3 of each side (M4 kernel), eps2 (Plummer).
 template <int SOFT>
-__global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void pair64(double rx, double ry, double rz, double mj, double hi,
+                                       double hinv_i, double hinv3_i, double hj, double hinv_j,
+                                       double hinv3_j, double eps2, double& fx, double& fy,
+                                       double& fz, double& fp) {
+  if (SOFT == KDFMM_SOFT_PLUMMER) {
+    const double r2 = rx * rx + ry * ry + rz * rz + eps2;
+    const double inv = rsqrt(r2);
+    const double minv = mj * inv;
+    const double f = minv * inv * inv;
+    fx -= f * rx; fy -= f * ry; fz -= f * rz;
+    fp -= minv;
+  } else {
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    if (r2 == 0.0) {
+      fp -= mj * 0.7 * (hinv_i + hinv_j);        // P(0) = 7/5 on both sides, halved
+      return;
+    }
+    const double inv = rsqrt(r2);
+    const double r = r2 * inv;
+    const double qa = r * hinv_i, qb = r * hinv_j;
+    double f, p;
+    if (qa < 2.0 || qb < 2.0) {
+      const double inv3 = inv * inv * inv;
+      const double fa = qa < 2.0 ? hinv3_i * m4_fq3_d(qa, hi * inv) : inv3;
+      const double fb = qb < 2.0 ? hinv3_j * m4_fq3_d(qb, hj * inv) : inv3;
+      const double pa = qa < 2.0 ? hinv_i * m4_pot_d(qa, hi * inv) : inv;
+      const double pb = qb < 2.0 ? hinv_j * m4_pot_d(qb, hj * inv) : inv;
+      f = 0.5 * (fa + fb);
+      p = 0.5 * (pa + pb);
+    } else {
+      f = inv * inv * inv;
+      p = inv;
+    }
+    const double mf = mj * f;
+    fx -= mf * rx; fy -= mf * ry; fz -= mf * rz;
+    fp -= mj * p;
+  }
+}
+
+// Float64 mode: lanes = (target, source slice) as K = 32 / n_t slices;
+// per chunk of near leaves (at most kStage64 sources) the warp stages the
+// sources' float64 positions, masses and smoothing lengths (with 1/h) in
+// shared memory, then every lane sums its slice; the target's own leaf is
+// summed separately (j != i).  The slices are added in slice order.
+template <int SOFT>
+__global__ void __launch_bounds__(kP2P64Warps * 32) k_p2p_fp64(P2PArgs A) {
+  constexpr bool M4 = SOFT == KDFMM_SOFT_M4;
+  __shared__ double s_x[kP2P64Warps][kStage64], s_y[kP2P64Warps][kStage64];
+  __shared__ double s_z[kP2P64Warps][kStage64], s_m[kP2P64Warps][kStage64];
+  __shared__ double s_h[M4 ? kP2P64Warps : 1][M4 ? kStage64 : 1];
+  __shared__ double s_hv[M4 ? kP2P64Warps : 1][M4 ? kStage64 : 1];
+  __shared__ uint8_t s_leaf[kP2P64Warps][kStage64];
+  __shared__ int s_tbeg[kP2P64Warps][32], s_tfirst[kP2P64Warps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
   const int nleaves = min(A.counters[C_LEAVES], A.max_leaves);
   const int nitems = nleaves + (int)min((int64_t)A.counters[C_SEGS], A.seg_cap);
-  for (int item = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); item < nitems;
-       item += (int)((gridDim.x * blockDim.x) >> 5)) {
+  double *sx = s_x[warp], *sy = s_y[warp], *sz = s_z[warp], *sm = s_m[warp];
+  double* sh = s_h[M4 ? warp : 0];
+  double* shv = s_hv[M4 ? warp : 0];
+  uint8_t* sl_of = s_leaf[warp];
+  int* tb = s_tbeg[warp];
+  int* tf = s_tfirst[warp];
+  for (int item = blockIdx.x * kP2P64Warps + warp; item < nitems; item += gridDim.x * kP2P64Warps) {
   const bool seg = item >= nleaves;
   const int g = item - nleaves;
   const int k = seg ? A.seg_leaf[g] : item;
@@ -502,30 +536,80 @@ __global__ void __launch_bounds__(256) k_p2p_fp64(P2PArgs A) {
   const int t = lane % nt, sl = lane / nt;
   const bool act = sl < K;
   const int64_t it = (int64_t)fa + t;
-  const double xi = A.tp.x[it], yi = A.tp.y[it], zi = A.tp.z[it], hi = A.tp.h[it];
+  const double xi = A.tp.x[it], yi = A.tp.y[it], zi = A.tp.z[it];
+  const double hi = M4 ? A.tp.h[it] : 0.0;
+  const double hinv_i = M4 ? 1.0 / hi : 0.0;
+  const double hinv3_i = hinv_i * hinv_i * hinv_i;
   const double eps = A.sys_eps[A.leaf_sys[k]];
   const double eps2 = eps * eps;
   double fx = 0.0, fy = 0.0, fz = 0.0, fp = 0.0;
+  if (!seg && act) {
+    for (int j = sl; j < nt; j += K) {
+      if (j == t) continue;
+      const int64_t js = (int64_t)fa + j;
+      const double hj = M4 ? A.tp.h[js] : 0.0;
+      const double hinv_j = M4 ? 1.0 / hj : 0.0;
+      pair64<SOFT>(xi - A.tp.x[js], yi - A.tp.y[js], zi - A.tp.z[js], A.tp.m[js], hi, hinv_i,
+                   hinv3_i, hj, hinv_j, hinv_j * hinv_j * hinv_j, eps2, fx, fy, fz, fp);
+    }
+  }
   const int64_t nall = min((int64_t)A.near_cnt[k], A.cap_near);
   const int64_t sidx = seg ? (int64_t)(g - A.seg_first[k] + 1) : 0;
-  const int64_t e0 = A.near_off[k] + sidx * kSegEntries;
   const int64_t e1 = A.near_off[k] + min(nall, (sidx + 1) * kSegEntries);
-  if (act) {
-    for (int64_t e = e0; e < e1; ++e) {
-      const int b = A.near_idx[e];
-      const int fb = A.cfirst[b], nb = A.ccount[b];
-      for (int j = sl; j < nb; j += K) {
-        if (b == a && j == t) continue;
-        const int64_t js = (int64_t)fb + j;
-        pair64<SOFT>(xi - A.tp.x[js], yi - A.tp.y[js], zi - A.tp.z[js], A.tp.m[js], hi, A.tp.h[js],
-                     eps2, fx, fy, fz, fp);
+  for (int64_t e = A.near_off[k] + sidx * kSegEntries; e < e1;) {
+    const int64_t my = e + lane;
+    int cnt = 0, first = 0;
+    if (my < e1) {
+      const int b = A.near_idx[my];
+      if (b != a) {
+        cnt = A.ccount[b];
+        first = A.cfirst[b];
       }
     }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int w = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += w;
+    }
+    const int L = __popc(__ballot_sync(full, my < e1 && incl <= kStage64));
+    if (lane < L) {
+      const int beg = incl - cnt;
+      tb[lane] = beg;
+      tf[lane] = first;
+      for (int q = 0; q < cnt; ++q) sl_of[beg + q] = (uint8_t)lane;
+    }
+    __syncwarp();
+    const int total = __shfl_sync(full, incl, L - 1);
+    for (int idx = lane; idx < total; idx += 32) {
+      const int l = sl_of[idx];
+      const int64_t src = (int64_t)tf[l] + idx - tb[l];
+      sx[idx] = A.tp.x[src];
+      sy[idx] = A.tp.y[src];
+      sz[idx] = A.tp.z[src];
+      sm[idx] = A.tp.m[src];
+      if (M4) {
+        const double h = A.tp.h[src];
+        sh[idx] = h;
+        shv[idx] = 1.0 / h;
+      }
+    }
+    __syncwarp();
+    if (act) {
+      for (int j = sl; j < total; j += K) {
+        double hj = 0.0, hinv_j = 0.0;
+        if (M4) { hj = sh[j]; hinv_j = shv[j]; }
+        pair64<SOFT>(xi - sx[j], yi - sy[j], zi - sz[j], sm[j], hi, hinv_i, hinv3_i, hj, hinv_j,
+                     hinv_j * hinv_j * hinv_j, eps2, fx, fy, fz, fp);
+      }
+    }
+    __syncwarp();
+    e += L;
   }
   for (int s = 1; s < K; ++s) {
     const int src = t + s * nt;
-    const double bx = __shfl_sync(0xffffffffu, fx, src), by = __shfl_sync(0xffffffffu, fy, src);
-    const double bz = __shfl_sync(0xffffffffu, fz, src), bp = __shfl_sync(0xffffffffu, fp, src);
+    const double bx = __shfl_sync(full, fx, src), by = __shfl_sync(full, fy, src);
+    const double bz = __shfl_sync(full, fz, src), bp = __shfl_sync(full, fp, src);
     if (sl == 0) { fx += bx; fy += by; fz += bz; fp += bp; }
   }
   if (sl != 0 || !act) continue;
@@ -677,15 +761,15 @@ int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s) {
   int rc = plan_segments(t, s);
   if (rc) return rc;
   const int gl = std::max(t->grid_leaves, 1);
-  const unsigned g = blocks_for((int64_t)gl * 32, 256);
   const bool m4 = t->p.soft_kind == KDFMM_SOFT_M4;
   if (t->p.precision == KDFMM_MIXED) {
     const unsigned gm = blocks_for(gl, kP2PWarps);
     if (m4) k_p2p_mixed<KDFMM_SOFT_M4><<<gm, kP2PWarps * 32, 0, s>>>(A);
     else k_p2p_mixed<KDFMM_SOFT_PLUMMER><<<gm, kP2PWarps * 32, 0, s>>>(A);
   } else {
-    if (m4) k_p2p_fp64<KDFMM_SOFT_M4><<<g, 256, 0, s>>>(A);
-    else k_p2p_fp64<KDFMM_SOFT_PLUMMER><<<g, 256, 0, s>>>(A);
+    const unsigned g64 = blocks_for(gl, kP2P64Warps);
+    if (m4) k_p2p_fp64<KDFMM_SOFT_M4><<<g64, kP2P64Warps * 32, 0, s>>>(A);
+    else k_p2p_fp64<KDFMM_SOFT_PLUMMER><<<g64, kP2P64Warps * 32, 0, s>>>(A);
   }
   k_seg_combine<<<152 * 2, 256, 0, s>>>(A);
   t->launches += 2;
