@@ -32,8 +32,6 @@ UNIT = "Mparticles/s"
 # Newtonian part: 3 sub, r^2 with 2 FMA + 1 mul + 1 add, rsqrt, 3 mul, 3 FMA,
 # potential add; FMA = 2 flops); the M4 kernel softening adds 10 per interaction
 P2P_FLOPS_PER_INTERACTION = {0: 20, 1: 30}
-# FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
 def log(*a):
@@ -83,9 +81,12 @@ def workload(args):
 # reference arm and CPU baseline: the oracle on a bounded sample
 # ---------------------------------------------------------------------------
 def oracle_rate(ps, args, budget_s, rng_seed=0):
-    """Oracle (single thread) on this workload: full tree build, forces of a
-    random sample of leaves until the budget is spent, extrapolated to all
-    leaves.  Returns (Mparticles/s, sample description)."""
+    """The oracle on this workload, as it stands: full tree build (one thread),
+    then forces of a random sample of leaves until the budget is spent,
+    extrapolated to all leaves -- once on one thread and once with the leaves
+    spread over every host core (OpenMP, same results bit for bit).  Returns
+    the two baselines and the sampled leaves' forces (caller order, NaN
+    outside the sample)."""
     import numpy as np
     import oracle
     oracle.build()
@@ -97,25 +98,37 @@ def oracle_rate(ps, args, budget_s, rng_seed=0):
     leaves = np.nonzero(c.is_leaf)[0]
     rng = np.random.default_rng(rng_seed)
     order = rng.permutation(leaves)
-    done, npart, t_eval, k = 0, 0, 0.0, 0
-    while t_eval < budget_s and k < len(order):
-        batch = order[k:k + 16]
-        t1 = time.perf_counter()
-        T.eval(leaves=np.sort(batch))
-        t_eval += time.perf_counter() - t1
-        npart += int(c.count[batch].sum())
-        done += len(batch)
-        k += len(batch)
-    t_total = t_build + t_eval * len(leaves) / done
-    desc = (f"oracle tree build of all {ps.n} particles ({t_build:.2f} s) + forces of {done} of "
-            f"{len(leaves)} leaves ({npart} particles, {t_eval:.2f} s), extrapolated to all leaves")
-    return ps.n / t_total / 1e6, desc, t_total
+    a_s = np.full((ps.n, 3), np.nan)
+    phi_s = np.full(ps.n, np.nan)
+    out = {}
+    k = 0
+    for label, threads in (("single", 1), ("all_cores", oracle.max_threads())):
+        done, npart, t_eval = 0, 0, 0.0
+        batch_n = 16 * threads
+        while t_eval < budget_s / 2 and k < len(order):
+            batch = np.sort(order[k:k + batch_n])
+            t1 = time.perf_counter()
+            a, phi = T.eval_threads(leaves=batch, nthreads=threads)
+            t_eval += time.perf_counter() - t1
+            rows = ~np.isnan(phi)
+            a_s[rows], phi_s[rows] = a[rows], phi[rows]
+            npart += int(c.count[batch].sum())
+            done += len(batch)
+            k += len(batch)
+        t_total = t_build + t_eval * len(leaves) / max(done, 1)
+        out[label] = {
+            "value": ps.n / t_total / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"oracle tree build of all {ps.n} particles ({t_build:.2f} s, one thread) + "
+                       f"forces of {done} random leaves of {len(leaves)} ({npart} particles, "
+                       f"{t_eval:.2f} s on {threads} thread(s)), extrapolated to all leaves")}
+    return out, a_s, phi_s
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import oracle
     ps, cfg = workload(args)
     per_step = max(1.0, min(6.0, 120.0 / max(1, args.steps + args.warmup)))
     rates = []
@@ -124,12 +137,13 @@ def run_reference(args):
         if k >= args.warmup:
             rates.append(r)
     value = statistics.mean(rates)
+    cores = oracle.max_threads()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ps.n / value / 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": cfg,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": _REF_DESC.get("desc", "")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -154,19 +168,21 @@ def oracle_rate_cached(ps, args, budget_s, seed):
     leaves = np.nonzero(c.is_leaf)[0]
     rng = np.random.default_rng(seed)
     order = rng.permutation(leaves)
+    threads = oracle.max_threads()
     done, npart, t_eval, k = 0, 0, 0.0, 0
     while t_eval < budget_s and k < len(order):
-        batch = order[k:k + 16]
+        batch = order[k:k + 16 * threads]
         t1 = time.perf_counter()
-        T.eval(leaves=np.sort(batch))
+        T.eval_threads(leaves=np.sort(batch), nthreads=threads)
         t_eval += time.perf_counter() - t1
         npart += int(c.count[batch].sum())
         done += len(batch)
         k += len(batch)
     t_total = t_build + t_eval * len(leaves) / done
     _REF_DESC["desc"] = (f"per step: forces of {done} random leaves of {len(leaves)} ({npart} "
-                         f"particles) timed and extrapolated to all leaves, plus the oracle's tree "
-                         f"build of all {ps.n} particles ({t_build:.2f} s)")
+                         f"particles) on {threads} host thread(s) (OpenMP over leaves) timed and "
+                         f"extrapolated to all leaves, plus the oracle's tree build of all {ps.n} "
+                         f"particles ({t_build:.2f} s, one thread)")
     return ps.n / t_total / 1e6, _REF_DESC["desc"], t_total
 
 
@@ -247,6 +263,32 @@ def traffic_for(kernel_key):
     if digest != rec.get("source_sha256"):
         return None
     return rec.get("bytes_per_launch_full_size")
+
+
+def rel_error_summary(a, phi, a_ref, phi_ref) -> dict:
+    """Per-particle relative errors |a - a_ref| / |a_ref| and |phi - phi_ref| /
+    |phi_ref|: maximum and root mean square."""
+    import numpy as np
+    na = np.linalg.norm(a_ref, axis=1)
+    ea = np.linalg.norm(a - a_ref, axis=1) / na
+    ep = np.abs(phi - phi_ref) / np.abs(phi_ref)
+    i = int(np.argmax(ea))
+    return {"a_max": float(ea.max()), "a_rms": float(np.sqrt(np.mean(ea ** 2))),
+            "a_p99999": float(np.quantile(ea, 0.99999)),
+            "a_worst_abs_a_over_median": float(na[i] / np.median(na)),
+            "a_n_above_2e-5": int(np.count_nonzero(ea > 2e-5)),
+            "phi_max": float(ep.max()), "phi_rms": float(np.sqrt(np.mean(ep ** 2)))}
+
+
+def total_force_summary(m, a_ref, F_mix, F64) -> dict:
+    """The method's uncompensated total force sum m a (Sec. 4) of both paths,
+    relative to sum m |a|, and the mixed path's deviation from the float64
+    one relative to |F_fp64|."""
+    import numpy as np
+    scale = float(np.sum(m * np.linalg.norm(a_ref, axis=1)))
+    return {"mixed": [float(v) for v in F_mix], "fp64_gpu": [float(v) for v in F64],
+            "fp64_rel_to_sum_m_abs_a": float(np.linalg.norm(F64) / scale),
+            "mixed_minus_fp64_rel": float(np.linalg.norm(F_mix - F64) / np.linalg.norm(F64))}
 
 
 def reduce_max(value: float, dev, world: int) -> float:
@@ -421,6 +463,9 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    # roofline denominators of this device: float32 peak derived from its SM
+    # count and maximum clock, and float32 / float64 FMA loops measured now
+    peaks = native.measure_peaks()
     ps, cfg = workload(args)
     cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
     n = ps.n
@@ -484,13 +529,20 @@ def run_ours(args):
     flops = st["np2p"] * P2P_FLOPS_PER_INTERACTION[ps.soft_kind]
     achieved = flops / (p2p_mean / 1e3) / 1e12
     kernel_key = f"k_p2p_{args.precision}_{'m4' if ps.soft_kind == 1 else 'plummer'}"
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic_for(kernel_key),
+    peak = peaks["fp32_derived_tflops"]
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_for(kernel_key),
                 "kernel": kernel_key, "flops_per_launch": flops,
                 "flops_per_interaction": P2P_FLOPS_PER_INTERACTION[ps.soft_kind],
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "peak_source": (f"derived: {peaks['sms']} SMs x 128 FP32 lanes x 2 flop x "
+                                f"{peaks['sm_max_mhz']:.0f} MHz (SM count and clock queried)"),
+                "peak_measured": peaks["fp32_tflops"],
+                "frac_of_measured": achieved / peaks["fp32_tflops"],
+                "peak_measured_source": "FFMA throughput loop in this run (kdfmm_measure_peaks)",
                 "launch_ms": p2p_mean}
     phase_mean = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+    # the mixed result of the last timed step, for the accuracy comparison
+    a_mix, phi_mix, F_mix = a.cpu().numpy(), phi.cpu().numpy(), F.cpu().numpy()
 
     # the plain FP64 GPU path on the same workload (the metric's comparison)
     fp64 = None
@@ -501,7 +553,8 @@ def run_ours(args):
         g.accel(a, phi)
         native.total_momentum(m, a, F)
         torch.cuda.synchronize()
-        t64 = []
+        native.tree_timing(g.handle, True, read=False)
+        t64, ph64 = [], []
         for _ in range(args.fp64_steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -513,9 +566,19 @@ def run_ours(args):
             e1.record(stream)
             e1.synchronize()
             t64.append(e0.elapsed_time(e1))
+            ph64.append(native.tree_timing(g.handle, True))
+        native.tree_timing(g.handle, False, read=False)
         ms64 = statistics.mean(t64)
+        phases64 = {k: statistics.mean(p[k] for p in ph64) for k in ph64[0]}
+        st64 = g.stats()
+        ach64 = st64["np2p"] * P2P_FLOPS_PER_INTERACTION[ps.soft_kind] / (phases64["p2p"] / 1e3) / 1e12
         fp64 = {"value": n / (ms64 / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms64,
-                "steps": args.fp64_steps}
+                "steps": args.fp64_steps, "phases_ms": phases64,
+                "p2p_roofline": {"bound": "alu", "achieved": ach64, "unit": "TFLOP/s",
+                                 "peak": peaks["fp64_tflops"], "frac": ach64 / peaks["fp64_tflops"],
+                                 "peak_source": "DFMA throughput loop in this run (kdfmm_measure_peaks)",
+                                 "kernel": f"k_p2p_fp64_{'m4' if ps.soft_kind == 1 else 'plummer'}"}}
+        a64, phi64, F64 = a.cpu().numpy(), phi.cpu().numpy(), F.cpu().numpy()
         del g
 
     # end to end through the public API from pinned host memory
@@ -556,7 +619,9 @@ def run_ours(args):
         ems = reduce_max(sum(te), dev, world)
         e2e = {"value": whole_job_rate(n, args.steps, ems, world), "unit": UNIT,
                "h2d_bytes_per_step": int(n * (24 + 8 + (8 if h is not None else 0))),
-               "d2h_bytes_per_step": int(n * 24 + 24), "ms_per_step": ems / args.steps}
+               "d2h_bytes_per_step": int(n * 24 + 24), "ms_per_step": ems / args.steps,
+               "path": ("public Python API (native.KdFmm over the C ABI) with torch copies from "
+                        "pinned host memory inside the timed events")}
 
     batched = None
     if args.batched_steps > 0:
@@ -568,10 +633,23 @@ def run_ours(args):
     if args.large_steps > 0 and rank == 0 and world == 1:
         large = run_large(args, dev, flush)
 
+    # accuracy of this run: mixed against the float64 GPU path (every
+    # particle) and both against the oracle on the baseline's sampled leaves
+    accuracy = None
+    if fp64 is not None:
+        accuracy = {"mixed_vs_fp64_gpu": rel_error_summary(a_mix, phi_mix, a64, phi64),
+                    "total_force": total_force_summary(ps.m, a64, F_mix, F64)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, desc, _ = oracle_rate(ps, args, args.cpu_budget_s)
-        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        base, a_or, phi_or = oracle_rate(ps, args, args.cpu_budget_s)
+        cpu = dict(base["all_cores"])
+        cpu["single_thread"] = base["single"]
+        if accuracy is not None:
+            rows = np.nonzero(~np.isnan(phi_or))[0]
+            accuracy["vs_oracle_sampled_leaves"] = {
+                "particles": int(rows.size),
+                "mixed": rel_error_summary(a_mix[rows], phi_mix[rows], a_or[rows], phi_or[rows]),
+                "fp64_gpu": rel_error_summary(a64[rows], phi64[rows], a_or[rows], phi_or[rows])}
 
     if rank == 0:
         line = {
@@ -587,6 +665,8 @@ def run_ours(args):
             "batched": batched,
             "variants": variants,
             "large": large,
+            "accuracy": accuracy,
+            "peaks": peaks,
             "interactions": {"p2p": st["np2p"], "m2l": st["nfar"], "nleaves": st["nleaves"],
                              "ncells": st["ncells"], "p2p_per_s": st["np2p"] / (ms_per_step / 1e3),
                              "m2l_per_s": st["nfar"] / (ms_per_step / 1e3)},

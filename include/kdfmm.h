@@ -239,6 +239,17 @@ int kdfmm_total_momentum(const double* m, const double* v, int64_t n, double* ou
 int kdfmm_total_momentum_noalloc(const double* m, const double* v, int64_t n, double* out,
                                  void* stream);
 
+/* Measurement utility (no counterpart in the paper): the roofline
+ * denominators of the ALU-bound kernels on the current device.  Runs two
+ * throughput loops on `stream` (independent fused multiply-add chains at full
+ * occupancy, best of three timed launches after one warm-up) and writes to
+ * out (host, 5 doubles): [0] float32 FMA TFLOP/s measured, [1] float64 FMA
+ * TFLOP/s measured, [2] SM count, [3] maximum SM clock in MHz, [4] float32
+ * peak derived as SMs x 128 lanes x 2 flop x maximum clock (TFLOP/s).
+ * Allocates and frees a small scratch buffer; synchronises the stream.
+ * NULL out gives KDFMM_ERR_INVALID_ARG. */
+int kdfmm_measure_peaks(double* out, void* stream);
+
 /* Host copies of the handle's statistics (KDFMM_NSTATS int64, host). */
 int kdfmm_tree_stats(kdfmm_tree t, int64_t* stats);
 

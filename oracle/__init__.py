@@ -35,7 +35,10 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math",
                "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
-        subprocess.check_call(cmd)
+        # OpenMP only spreads orc_eval_threads' leaves over host cores; without
+        # it that entry point runs on one thread
+        if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+            subprocess.check_call(cmd)
         os.replace(_LIB + ".tmp", _LIB)
     return _LIB
 
@@ -68,6 +71,10 @@ def _load():
     L.orc_lists_free.argtypes = [P]
     L.orc_eval.restype = i32
     L.orc_eval.argtypes = [P, i32, P, P, P, P, P, P, P, P]
+    L.orc_eval_threads.restype = i32
+    L.orc_eval_threads.argtypes = [P, i32, P, P, P, i32]
+    L.orc_max_threads.restype = i32
+    L.orc_max_threads.argtypes = []
     L.orc_eval_lists.restype = i32
     L.orc_eval_lists.argtypes = [P, i32, P, P, P, P, P, P, P]
     L.orc_moments_frozen.restype = i32
@@ -246,6 +253,20 @@ class Tree:
         return a, phi
 
 
+    def eval_threads(self, leaves=None, nthreads: int = 0):
+        """eval() with the leaves spread over host threads (OpenMP); the same
+        a and phi bit for bit."""
+        a = np.full((self.n, 3), np.nan)
+        phi = np.full(self.n, np.nan)
+        if leaves is None:
+            rc = _load().orc_eval_threads(self._t, -1, None, _p(a), _p(phi), int(nthreads))
+        else:
+            sel = np.ascontiguousarray(leaves, dtype=np.int32)
+            rc = _load().orc_eval_threads(self._t, len(sel), _p(sel), _p(a), _p(phi), int(nthreads))
+        if rc != 0:
+            raise ValueError(f"oracle eval_threads failed ({rc})")
+        return a, phi
+
     def dual_walk(self) -> "DualLists":
         """Lists of the symmetric dual-tree walk: far list of every cell (ids in
         ascending order), near list of every leaf (leaves in ascending id)."""
@@ -301,6 +322,11 @@ class Tree:
         if rc != 0:
             raise ValueError(f"oracle eval_lists failed ({rc})")
         return a, phi
+
+
+def max_threads() -> int:
+    """Host threads eval_threads uses by default."""
+    return int(_load().orc_max_threads())
 
 
 def direct(x, m, h=None, *, soft_kind=SOFT_PLUMMER, eps=0.01, targets=None):

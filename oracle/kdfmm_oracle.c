@@ -57,6 +57,11 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#else
+static int omp_get_max_threads(void) { return 1; }
+#endif
 
 static const double KD_PI = 3.14159265358979323846;
 
@@ -543,7 +548,10 @@ static void walk_rec(const otree* T, int32_t alpha, int32_t beta, ivec* far, ive
             walk_rec(T, alpha, b->right, far, near);
         }
     } else {
-        if (a->first >= b->first && a->first < b->first + b->count) g_ancestor_far++;
+        if (a->first >= b->first && a->first < b->first + b->count) {
+#pragma omp atomic
+            g_ancestor_far++;
+        }
         ivec_push(far, beta);
     }
 }
@@ -672,6 +680,45 @@ int32_t orc_eval(const otree* T, int32_t nsel, const int32_t* sel, double* a, do
     }
     if (stats) { stats[0] = npp; stats[1] = nm2l; }
     return 0;
+}
+
+/* orc_eval for the selected leaves (all when nsel < 0) with the leaves
+ * spread over OpenMP threads when compiled with OpenMP (nthreads <= 0: the
+ * OpenMP default).  Each leaf's walk and sums are the same steps as in
+ * orc_eval and write only that leaf's particles, so a and phi are orc_eval's
+ * bit for bit.  Used to time the oracle on every host core. */
+int32_t orc_eval_threads(const otree* T, int32_t nsel, const int32_t* sel, double* a, double* phi,
+                         int32_t nthreads) {
+    jet_init();
+    int32_t nl = nsel < 0 ? T->ncells : nsel;
+    for (int32_t t = 0; t < nl; ++t) {
+        int32_t alpha = nsel < 0 ? t : sel[t];
+        if (alpha < 0 || alpha >= T->ncells) return -1;
+        if (T->cells[alpha].left >= 0 && nsel >= 0) return -2;
+    }
+    (void)nthreads;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
+    for (int32_t t = 0; t < nl; ++t) {
+        int32_t alpha = nsel < 0 ? t : sel[t];
+        if (T->cells[alpha].left >= 0) continue;
+        int64_t npp = 0;
+        ivec far = {0}, near = {0};
+        walk_rec(T, alpha, 0, &far, &near);
+        eval_leaf(T, alpha, far.v, far.n, near.v, near.n, a, phi, NULL, NULL, NULL, NULL, &npp);
+        free(far.v);
+        free(near.v);
+    }
+    return 0;
+}
+
+/* Threads an OpenMP parallel region of orc_eval_threads would use (1 without
+ * OpenMP). */
+int32_t orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* Evaluation with given interaction lists (frozen topology): leaf_ids[k] is

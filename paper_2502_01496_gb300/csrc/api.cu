@@ -64,6 +64,24 @@ int set_error(int code, const char* fmt, ...) {
   return code;
 }
 
+int sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 1;
+    }
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
 int check_cuda(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return KDFMM_OK;
   return set_error(KDFMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));

@@ -1449,7 +1449,7 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
   if ((rc = subtree_setup(t, smem))) return rc;
   const int gsub = deferred ? t->subtree_grid : std::max(1, std::min(t->subtree_grid, hc[C_NB]));
   k_subtree<<<gsub, kSubtreeThreads, smem, s>>>(S);
-  k_leaf_segs<<<kGridBlocks / 4, 128, 0, s>>>(S, t->segL);
+  k_leaf_segs<<<grid_blocks(2), 128, 0, s>>>(S, t->segL);
   t->launches += 2;
   if (!deferred) {
     if ((rc = read_back("build subtrees"))) return rc;
@@ -1463,14 +1463,14 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
 
   // pre-order numbering, counts read on the device
   k_fill2<<<blocks_for(n + 1, 256), 256, 0, s>>>(t->cnt_start, 0, t->min_depth, INT_MAX, n + 1);
-  k_count_starts<<<kGridBlocks, 256, 0, s>>>(t->tmp, t->counters, t->cnt_start, t->min_depth);
+  k_count_starts<<<grid_blocks(), 256, 0, s>>>(t->tmp, t->counters, t->cnt_start, t->min_depth);
   scan_i32(t->cnt_start, t->start_off, n, t->scan_tmp, s);
-  k_remap<<<kGridBlocks, 256, 0, s>>>(t->tmp, t->counters, t->start_off, t->min_depth, t->c,
+  k_remap<<<grid_blocks(), 256, 0, s>>>(t->tmp, t->counters, t->start_off, t->min_depth, t->c,
                                       t->status);
-  k_leaf_flags<<<kGridBlocks, 256, 0, s>>>(t->c, t->counters, t->c.ready);
+  k_leaf_flags<<<grid_blocks(), 256, 0, s>>>(t->c, t->counters, t->c.ready);
   scan_i32_dev(t->c.ready, t->leaf_rank, t->counters + C_CELLS,
                deferred ? t->cap_cells : (int64_t)t->ncells, t->scan_tmp, s);
-  k_leaf_list<<<kGridBlocks, 256, 0, s>>>(t->c, t->counters, t->leaf_rank, t->leaf_cells,
+  k_leaf_list<<<grid_blocks(), 256, 0, s>>>(t->c, t->counters, t->leaf_rank, t->leaf_cells,
                                           t->sys_off, t->n_sys, t->leaf_sys);
   k_sys_roots<<<blocks_for(t->n_sys + 1, 128), 128, 0, s>>>(t->sys_off, t->n_sys, t->start_off,
                                                             t->sys_root);
@@ -1485,8 +1485,8 @@ int build_tree(kdfmm_tree_s* t, const double* x, const double* m, const double* 
   // known leaf count with a margin; more leaves than threads loop
   const int64_t up_threads = std::max<int64_t>(t->nleaves, 1) + t->nleaves / 4 + 128;
   k_upward<<<blocks_for(up_threads, 128), 128, 0, s>>>(t->c, t->leaf_cells, t->counters, t->tp);
-  k_derive_cells<<<kGridBlocks, 256, 0, s>>>(t->c, t->counters, t->com_bound);
-  k_particles32<<<kGridBlocks, 256, 0, s>>>(t->c, t->leaf_cells, t->counters, t->tp, t->pf, t->ph);
+  k_derive_cells<<<grid_blocks(), 256, 0, s>>>(t->c, t->counters, t->com_bound);
+  k_particles32<<<grid_blocks(), 256, 0, s>>>(t->c, t->leaf_cells, t->counters, t->tp, t->pf, t->ph);
   t->launches += 15;
   return check_cuda(cudaGetLastError(), "build launch");
 }
@@ -1653,8 +1653,8 @@ int recompute_moments(kdfmm_tree_s* t, const double* x, const double* m, const d
   cudaMemsetAsync(t->c.ready, 0, (size_t)ncells * sizeof(int32_t), s);
   k_upward_frozen<<<blocks_for(nl, 128), 128, 0, s>>>(t->c, t->leaf_cells, nl, Sx, Sy, Sz);
   k_size_frozen<<<blocks_for((int64_t)ncells * 32, 256), 256, 0, s>>>(t->c, ncells, t->tp);
-  k_derive_cells<<<kGridBlocks, 256, 0, s>>>(t->c, t->counters, t->com_bound);
-  k_particles32<<<kGridBlocks, 256, 0, s>>>(t->c, t->leaf_cells, t->counters, t->tp,
+  k_derive_cells<<<grid_blocks(), 256, 0, s>>>(t->c, t->counters, t->com_bound);
+  k_particles32<<<grid_blocks(), 256, 0, s>>>(t->c, t->leaf_cells, t->counters, t->tp,
                                                                   t->pf, t->ph);
   t->launches += 6;
   cudaMemcpyAsync(&t->host_counters[16], t->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);

@@ -33,7 +33,6 @@ namespace {
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 constexpr int kLevelsPerSync = 8;
-constexpr unsigned kLevelGrid = 152 * 8;
 
 enum { DQ_OUT = 0, DQ_FAR = 1, DQ_NEAR = 2, DQ_OVER = 3, DQ_IN = 4 };
 
@@ -420,7 +419,7 @@ int run_dual_walk(kdfmm_tree_s* t, cudaStream_t s) {
         A.in = D.q[cur];
         A.out = D.q[cur ^ 1];
         k_dual_advance<<<1, 1, 0, s>>>(D.ctr);
-        k_dual_level<<<kLevelGrid, 256, 0, s>>>(A);
+        k_dual_level<<<grid_blocks(), 256, 0, s>>>(A);
         t->launches += 2;
         cur ^= 1;
       }
@@ -489,7 +488,7 @@ int run_dual_local(kdfmm_tree_s* t, cudaStream_t s) {
   A.tot = D.ltot;
   A.leaf32 = t->lexp32;
   A.leaf64 = t->lexp64;
-  const unsigned grid = std::min<unsigned>(blocks_for(std::max(t->ncells, 1), 128), kGridBlocks);
+  const unsigned grid = std::min<unsigned>(blocks_for(std::max(t->ncells, 1), 128), grid_blocks());
   for (int level = 0; level <= t->depth; ++level) {
     A.level = level;
     k_l2l_level<<<grid, 128, 0, s>>>(A);

@@ -42,7 +42,7 @@ extern "C" int kdfmm_kick_drift(double* x, double* v, const double* a, int64_t n
     }
   }
   const int64_t n3 = 3 * n;
-  const unsigned blocks = (unsigned)std::min<int64_t>((n3 + 255) / 256, 152 * 16);
+  const unsigned blocks = (unsigned)std::min<int64_t>((n3 + 255) / 256, grid_blocks(16));
   k_kick_drift<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, v, a, n3, dt_kick,
                                                                        dt_drift);
   return check_cuda(cudaGetLastError(), "kick_drift launch");

@@ -47,8 +47,10 @@ enum : int {
   C_SEGS = 14,      // extra P2P segments of leaves with long near lists
 };
 
-// Grid of the grid-stride (persistent) kernels: blocks per SM x SMs of a GB300.
-constexpr int kGridBlocks = 152 * 8;
+// Streaming multiprocessors of the current device (queried once per device).
+int sm_count();
+// Grid of the grid-stride (persistent) kernels: per_sm blocks on every SM.
+inline unsigned grid_blocks(int per_sm = 8) { return (unsigned)(sm_count() * per_sm); }
 #define KD_GRID_STRIDE(i, n)                                                             \
   for (int i = (int)(blockIdx.x * blockDim.x + threadIdx.x); i < (n); i += (int)(gridDim.x * blockDim.x))
 

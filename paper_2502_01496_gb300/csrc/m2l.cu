@@ -21,9 +21,14 @@
 // dropping the quadrupole's C2 and C3 terms (template flag STD).
 //
 // One warp per sink leaf; its lanes take the far cells in turn.  Mixed mode
-// works in float32 with the centre-of-mass difference formed from
-// (high, low) float pairs and compensated sums for C0 and C1; FP64 mode works
-// in float64 throughout.
+// works in float32, except the monopole's share of C0 and C1 (-M/R and
+// M R/R^3, the terms that carry the forces between cells and so the total
+// force of Sec. 4): those are formed in float-float arithmetic (error-free
+// products with FMA, compensated R^2, one Newton step on the reciprocal
+// square root) from R = com_alpha - com_beta taken exactly from the (high,
+// low) float centres, and C0 and C1 are summed with compensation.  Plain
+// float32 there left a total force 1e-3 off the float64 one at theta = 0.3.
+// FP64 mode works in float64 throughout.
 #include <algorithm>
 #include <climits>
 
@@ -39,6 +44,60 @@ template <>
 __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
 template <>
 __device__ __forceinline__ double rsqrt_t<double>(double v) { return 1.0 / sqrt(v); }
+
+// Error-free transforms (float32): a * b = p + e exactly (FMA), and the
+// float-float monopole of a far cell: C0 = -M / R and C1 = M R / R^3 as
+// (high, low) pairs from R = (Rh + Rl).
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+__device__ __forceinline__ void monopole_ff(const float Rh[3], const float Rl[3], float M,
+                                            float C0[2], float C1[3][2]) {
+  // R^2 = S + sl
+  float p0, e0, p1, e1, p2, e2;
+  two_prod(Rh[0], Rh[0], p0, e0);
+  two_prod(Rh[1], Rh[1], p1, e1);
+  two_prod(Rh[2], Rh[2], p2, e2);
+  float S, t, S2, t2;
+  two_sum(p0, p1, S, t);
+  two_sum(S, p2, S2, t2);
+  const float sl = (t + t2) + (e0 + e1 + e2) +
+                   2.0f * fmaf(Rh[0], Rl[0], fmaf(Rh[1], Rl[1], Rh[2] * Rl[2]));
+  // y = 1 / sqrt(S2 + sl) = yh + yl: one Newton step on the hardware estimate
+  const float y0 = rsqrtf(S2);
+  float q, qe;
+  two_prod(y0, y0, q, qe);
+  const float res = fmaf(-S2, q, 1.0f) - (S2 * qe + sl * q);   // 1 - R^2 y0^2
+  const float yl = 0.5f * y0 * res;
+  float yh, yl2;
+  fast_two_sum(y0, yl, yh, yl2);
+  // y^3 = (y^2) y
+  float y2, y2e;
+  two_prod(yh, yh, y2, y2e);
+  y2e += 2.0f * yh * yl2;
+  float y3, y3e;
+  two_prod(y2, yh, y3, y3e);
+  y3e += y2 * yl2 + y2e * yh;
+  // M y^3 and M y
+  float my3, my3e, my, mye;
+  two_prod(M, y3, my3, my3e);
+  my3e = fmaf(M, y3e, my3e);
+  two_prod(M, yh, my, mye);
+  mye = fmaf(M, yl2, mye);
+  C0[0] = -my; C0[1] = -mye;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float c, ce;
+    two_prod(my3, Rh[i], c, ce);
+    C1[i][0] = c;
+    C1[i][1] = ce + fmaf(my3, Rl[i], my3e * Rh[i]);
+  }
+}
 
 template <class T>
 __device__ __forceinline__ T c2e(int a, int b, const T R[3], const T u[3], const T Qm[3][3], T s1,
@@ -63,7 +122,8 @@ __device__ __forceinline__ T c3e(int a, int b, int c, const T R[3], const T u[3]
 // STD: the standard p = 3 series (sink and source orders add up to at most
 // p - 1 = 2 for the acceleration): the quadrupole keeps only its C0 and C1
 // terms, C2 and C3 come from the monopole alone.
-template <class T, bool STD = false>
+// NOMONO01: leave the monopole's share out of C0 and C1 (added separately).
+template <class T, bool STD = false, bool NOMONO01 = false>
 __device__ __forceinline__ void m2l_coeffs(T Rx, T Ry, T Rz, T M, const T Q[6], T out[20]) {
   const T R[3] = {Rx, Ry, Rz};
   const T Qm[3][3] = {{Q[0], Q[1], Q[2]}, {Q[1], Q[3], Q[4]}, {Q[2], Q[4], Q[5]}};
@@ -83,9 +143,9 @@ __device__ __forceinline__ void m2l_coeffs(T Rx, T Ry, T Rz, T M, const T Q[6], 
   const T qs = q * sixth;
   const T s1 = -M * g1 - g3 * qs;
   const T t2 = -g2 * third;
-  out[0] = -M * g0 - g2 * qs;
+  out[0] = (NOMONO01 ? T(0) : -M * g0) - g2 * qs;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) out[1 + i] = s1 * R[i] + t2 * u[i];
+  for (int i = 0; i < 3; ++i) out[1 + i] = (NOMONO01 ? -g3 * qs : s1) * R[i] + t2 * u[i];
   // second and third order: both parts, or the monopole alone (STD)
   const T s1h = STD ? -M * g1 : s1;
   const T s2 = STD ? -M * g2 : -M * g2 - g4 * qs;
@@ -148,14 +208,30 @@ __global__ void __launch_bounds__(128) k_m2l_mixed(M2LArgs A) {
     const int b = A.far_idx[off + e];
     const float4 b0 = A.src32[4 * b], b1 = A.src32[4 * b + 1], b2 = A.src32[4 * b + 2],
                  b3 = A.src32[4 * b + 3];
-    const float Rx = (ah.x - b0.x) + (al.x - b1.x);
-    const float Ry = (ah.y - b0.y) + (al.y - b1.y);
-    const float Rz = (ah.z - b0.z) + (al.z - b1.z);
+    // R = com_alpha - com_beta as (high, low) from the (high, low) centres
+    float Rh[3], Rl[3];
+    {
+      const float ahv[3] = {ah.x, ah.y, ah.z}, alv[3] = {al.x, al.y, al.z};
+      const float bhv[3] = {b0.x, b0.y, b0.z}, blv[3] = {b1.x, b1.y, b1.z};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float d, e;
+        two_sum(ahv[i], -bhv[i], d, e);
+        fast_two_sum(d, (alv[i] - blv[i]) + e, Rh[i], Rl[i]);
+      }
+    }
     const float Q[6] = {b2.x, b2.y, b2.z, b2.w, b3.x, b3.y};
     float C[20];
-    m2l_coeffs<float, STD>(Rx, Ry, Rz, b0.w, Q, C);
+    m2l_coeffs<float, STD, true>(Rh[0], Rh[1], Rh[2], b0.w, Q, C);
+    float C0[2], C1[3][2];
+    monopole_ff(Rh, Rl, b0.w, C0, C1);
+    df_add2(acc[0], lo[0], C0[0], C0[1]);
+    df_add(acc[0], lo[0], C[0]);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) df_add(acc[j], lo[j], C[j]);
+    for (int j = 1; j < 4; ++j) {
+      df_add2(acc[j], lo[j], C1[j - 1][0], C1[j - 1][1]);
+      df_add(acc[j], lo[j], C[j]);
+    }
 #pragma unroll
     for (int j = 4; j < 20; ++j) acc[j] += C[j];
   }

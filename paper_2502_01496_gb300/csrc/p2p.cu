@@ -723,7 +723,7 @@ int64_t segments_bound(const kdfmm_tree_s* t) {
 int plan_segments(kdfmm_tree_s* t, cudaStream_t s) {
   const int gl = std::max(t->grid_leaves, 1);
   cudaMemsetAsync(t->counters + C_SEGS, 0, sizeof(int32_t), s);
-  k_seg_plan<<<std::min<unsigned>(blocks_for(gl, 256), kGridBlocks), 256, 0, s>>>(
+  k_seg_plan<<<std::min<unsigned>(blocks_for(gl, 256), grid_blocks()), 256, 0, s>>>(
       t->L.near_cnt, t->L.exact ? INT64_MAX : t->L.cap_near, gl, t->counters, t->L.seg_first,
       t->L.seg_leaf, t->L.seg_cap, t->status);
   t->launches += 1;
@@ -771,7 +771,7 @@ int run_p2p(kdfmm_tree_s* t, double* a, double* phi, cudaStream_t s) {
     if (m4) k_p2p_fp64<KDFMM_SOFT_M4><<<g64, kP2P64Warps * 32, 0, s>>>(A);
     else k_p2p_fp64<KDFMM_SOFT_PLUMMER><<<g64, kP2P64Warps * 32, 0, s>>>(A);
   }
-  k_seg_combine<<<152 * 2, 256, 0, s>>>(A);
+  k_seg_combine<<<grid_blocks(2), 256, 0, s>>>(A);
   t->launches += 2;
   return check_cuda(cudaGetLastError(), "p2p launch");
 }

@@ -617,7 +617,7 @@ int run_vjp(kdfmm_tree_s* t, const double* a_bar, double* x_bar, double* m_bar, 
     else k_vjp_m2l<false, double><<<gw, 128, 0, s>>>(V);
     k_vjp_p2p<double><<<gw, 128, 0, s>>>(V);
   }
-  k_vjp_seg_combine<<<152 * 2, 256, 0, s>>>(V);
+  k_vjp_seg_combine<<<grid_blocks(2), 256, 0, s>>>(V);
   k_vjp_moments<<<blocks_for(nl, 128), 128, 0, s>>>(V);
   k_scatter_bar<<<blocks_for(n, 256), 256, 0, s>>>(V, x_bar, m_bar);
   t->launches += 7;

@@ -362,7 +362,6 @@ constexpr int kHeavyThreads = 256;
 constexpr int kHeavyPer = 4;                        // consecutive cells per thread
 constexpr int kHeavyTile = kHeavyThreads * kHeavyPer;
 constexpr int kHeavyWarps = kHeavyThreads / 32;
-constexpr int kHeavyGrid = 152 * 2;
 
 // Exclusive block scan (maximum) of v; *total gets the block's maximum.
 __device__ __forceinline__ int block_excl_max(int v, int* total, int* sh) {
@@ -610,16 +609,13 @@ static bool list_mode_is(const char* want) {
 // Persistent grid of the arena walk: the resident blocks, at most one thread
 // per leaf.
 static int arena_grid_for(int leaves) {
-  static int per_sm = 0, sms = 0;
+  static int per_sm = 0;
+  const int sms = sm_count();
   if (per_sm == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_arena, 128, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_arena, 128, 0) != cudaSuccess ||
         per_sm < 1) {
       cudaGetLastError();
       per_sm = 1;
-      sms = 152;
     }
   }
   return (int)std::max<int64_t>(1, std::min<int64_t>(blocks_for(std::max(leaves, 1), 128),
@@ -675,12 +671,12 @@ static void walk_launch(kdfmm_tree_s* t, WalkArgs W, ListMode mode, int64_t cf, 
   cudaMemsetAsync(t->counters + C_HEAVY, 0, sizeof(int32_t), s);
   if (arena) {
     k_walk_arena<<<L.arena_grid, 128, 0, s>>>(W);
-    k_arena_copy<<<kGridBlocks, 256, 0, s>>>(W, (int64_t)L.arena_grid * 128);
+    k_arena_copy<<<grid_blocks(), 256, 0, s>>>(W, (int64_t)L.arena_grid * 128);
     t->launches += 1;
   } else {
     k_walk<<<blocks_for(std::max(slot_leaves, 1), 128), 128, 0, s>>>(W);
   }
-  k_walk_heavy<<<kHeavyGrid, kHeavyThreads, 0, s>>>(W);
+  k_walk_heavy<<<grid_blocks(2), kHeavyThreads, 0, s>>>(W);
   t->launches += 2;
 }
 

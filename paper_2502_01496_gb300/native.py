@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
                                           P, P, P]
     L.kdfmm_kick_drift.argtypes = [P, P, P, i64, ctypes.c_double, ctypes.c_double, P]
     L.kdfmm_tree_timing.argtypes = [P, ctypes.c_int, P]
+    L.kdfmm_measure_peaks.argtypes = [P, P]
     L.kdfmm_tree_timing.restype = i32
     L.kdfmm_last_error.restype = ctypes.c_char_p
     L.kdfmm_last_error.argtypes = []
@@ -288,6 +289,16 @@ def tree_timing(tree, enable: bool = True, read: bool = True) -> dict | None:
                                    None if ms is None else ms.ctypes.data_as(ctypes.c_void_p)),
            "tree_timing")
     return None if ms is None else {k: float(v) for k, v in zip(PHASES, ms)}
+
+
+def measure_peaks(stream=None) -> dict:
+    """Measured float32 / float64 FMA throughput of the current device and the
+    derived float32 peak (see kdfmm_measure_peaks)."""
+    out = np.zeros(5, dtype=np.float64)
+    _check(lib().kdfmm_measure_peaks(out.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+           "measure_peaks")
+    return {"fp32_tflops": float(out[0]), "fp64_tflops": float(out[1]), "sms": int(out[2]),
+            "sm_max_mhz": float(out[3]), "fp32_derived_tflops": float(out[4])}
 
 
 @dataclass

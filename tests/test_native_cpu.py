@@ -74,3 +74,9 @@ def test_forest_arguments_are_checked_on_the_host(libpath):
     assert call([0, 5, 9], theta=[0.5, 1.5]) == -1 and "theta[1]" in native.last_error()
     assert call([0, 5, 9], nleaf=[16, 33]) == -1 and "n_leaf[1]" in native.last_error()
     assert call([0, 5, 9]) == -1 and "tree is NULL" in native.last_error()
+
+
+def test_measure_peaks_rejects_null_output_without_a_gpu(libpath):
+    from paper_2502_01496_gb300 import native
+    assert native.lib().kdfmm_measure_peaks(None, None) == -1
+    assert "NULL" in native.last_error()
