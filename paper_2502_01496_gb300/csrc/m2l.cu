@@ -43,7 +43,7 @@ __device__ __forceinline__ T rsqrt_t(T v);
 template <>
 __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
 template <>
-__device__ __forceinline__ double rsqrt_t<double>(double v) { return 1.0 / sqrt(v); }
+__device__ __forceinline__ double rsqrt_t<double>(double v) { return rsqrt(v); }
 
 // Error-free transforms (float32): a * b = p + e exactly (FMA), and the
 // float-float monopole of a far cell: C0 = -M / R and C1 = M R / R^3 as

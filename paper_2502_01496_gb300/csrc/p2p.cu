@@ -503,7 +503,7 @@ __device__ __forceinline__ void pair64(double rx, double ry, double rz, double m
 
 // Float64 mode: lanes = (target, source slice) as K = 32 / n_t slices;
 // per chunk of near leaves (at most kStage64 sources) the warp stages the
-// sources' float64 positions, masses and smoothing lengths (with 1/h) in
+// sources' float64 positions, masses and smoothing lengths (with (2h)^2) in
 // shared memory, then every lane sums its slice; the target's own leaf is
 // summed separately (j != i).  The slices are added in slice order.
 template <int SOFT>
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(kP2P64Warps * 32) k_p2p_fp64(P2PArgs A) {
   __shared__ double s_x[kP2P64Warps][kStage64], s_y[kP2P64Warps][kStage64];
   __shared__ double s_z[kP2P64Warps][kStage64], s_m[kP2P64Warps][kStage64];
   __shared__ double s_h[M4 ? kP2P64Warps : 1][M4 ? kStage64 : 1];
-  __shared__ double s_hv[M4 ? kP2P64Warps : 1][M4 ? kStage64 : 1];
+  __shared__ double s_h2[M4 ? kP2P64Warps : 1][M4 ? kStage64 : 1];   // (2 h)^2, rounded up
   __shared__ uint8_t s_leaf[kP2P64Warps][kStage64];
   __shared__ int s_tbeg[kP2P64Warps][32], s_tfirst[kP2P64Warps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(kP2P64Warps * 32) k_p2p_fp64(P2PArgs A) {
   const int nitems = nleaves + (int)min((int64_t)A.counters[C_SEGS], A.seg_cap);
   double *sx = s_x[warp], *sy = s_y[warp], *sz = s_z[warp], *sm = s_m[warp];
   double* sh = s_h[M4 ? warp : 0];
-  double* shv = s_hv[M4 ? warp : 0];
+  double* sh2 = s_h2[M4 ? warp : 0];
   uint8_t* sl_of = s_leaf[warp];
   int* tb = s_tbeg[warp];
   int* tf = s_tfirst[warp];
@@ -540,6 +540,7 @@ __global__ void __launch_bounds__(kP2P64Warps * 32) k_p2p_fp64(P2PArgs A) {
   const double hi = M4 ? A.tp.h[it] : 0.0;
   const double hinv_i = M4 ? 1.0 / hi : 0.0;
   const double hinv3_i = hinv_i * hinv_i * hinv_i;
+  const double h2i = 4.0 * hi * hi * (1.0 + 1e-12);
   const double eps = A.sys_eps[A.leaf_sys[k]];
   const double eps2 = eps * eps;
   double fx = 0.0, fy = 0.0, fz = 0.0, fp = 0.0;
@@ -591,16 +592,44 @@ __global__ void __launch_bounds__(kP2P64Warps * 32) k_p2p_fp64(P2PArgs A) {
       if (M4) {
         const double h = A.tp.h[src];
         sh[idx] = h;
-        shv[idx] = 1.0 / h;
+        sh2[idx] = 4.0 * h * h * (1.0 + 1e-12);
       }
     }
     __syncwarp();
-    if (act) {
-      for (int j = sl; j < total; j += K) {
-        double hj = 0.0, hinv_j = 0.0;
-        if (M4) { hj = sh[j]; hinv_j = shv[j]; }
-        pair64<SOFT>(xi - sx[j], yi - sy[j], zi - sz[j], sm[j], hi, hinv_i, hinv3_i, hj, hinv_j,
-                     hinv_j * hinv_j * hinv_j, eps2, fx, fy, fz, fp);
+    if (act && !M4) {
+      for (int j = sl; j < total; j += K)
+        pair64<SOFT>(xi - sx[j], yi - sy[j], zi - sz[j], sm[j], 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, eps2,
+                     fx, fy, fz, fp);
+    } else if (act) {
+      // M4 kernel, 32 sources of the lane's slice at a time.  Pass 1: every
+      // pair as 1/r^2 except those that may lie inside either support
+      // (r^2 < (2 max(h_i, h_j))^2, thresholds rounded up), which are marked;
+      // pass 2: the marked pairs with the full symmetrised pair.  A warp
+      // branching per pair instead ran the kernel path for all its lanes
+      // whenever one lane needed it.
+      for (int j0 = sl; j0 < total; j0 += 32 * K) {
+        uint32_t in = 0u;
+        for (int b = 0; b < 32; ++b) {
+          const int j = j0 + b * K;
+          if (j >= total) break;
+          const double rx = xi - sx[j], ry = yi - sy[j], rz = zi - sz[j];
+          const double r2 = rx * rx + ry * ry + rz * rz;
+          const bool inside = r2 < fmax(h2i, sh2[j]);
+          in |= (uint32_t)inside << b;
+          const double inv = rsqrt(inside ? 1.0 : r2);
+          const double minv = (inside ? 0.0 : sm[j]) * inv;
+          const double f = minv * inv * inv;
+          fx -= f * rx; fy -= f * ry; fz -= f * rz;
+          fp -= minv;
+        }
+        while (in != 0u) {
+          const int b = __ffs(in) - 1;
+          in &= in - 1u;
+          const int j = j0 + b * K;
+          const double hj = sh[j], hinv_j = 1.0 / hj;
+          pair64<SOFT>(xi - sx[j], yi - sy[j], zi - sz[j], sm[j], hi, hinv_i, hinv3_i, hj, hinv_j,
+                       hinv_j * hinv_j * hinv_j, eps2, fx, fy, fz, fp);
+        }
       }
     }
     __syncwarp();
