@@ -266,6 +266,17 @@ int kdfmm_tree_export(kdfmm_tree t, int64_t* perm, int64_t* cell_ints, double* c
                       int32_t* leaf_ids, int64_t* far_off, int32_t* far_idx, int64_t* near_off,
                       int32_t* near_idx);
 
+/* Tuning (no counterpart in the paper): the number of cells one thread of the
+ * leaf walk visits before it hands its leaf to the block-wide walk, which
+ * decides every cell of the leaf's system in tiles of 1024 (a leaf in the
+ * sparse outskirts of a condensed system can open most of the tree).  budget
+ * = 0 restores the default (KDFMM_WALK_BUDGET from the environment, else
+ * 4096).  Interaction lists and forces do not depend on it; the arena walk's
+ * scratch grows with it (budget x 4 bytes per walk thread).  Takes effect at
+ * the next evaluation (a captured batch graph is captured again).  budget
+ * outside [0, 2^20] or a NULL handle gives KDFMM_ERR_INVALID_ARG. */
+int kdfmm_tree_set_walk_budget(kdfmm_tree t, int32_t budget);
+
 /* Tracing (no counterpart in the paper): with enable = 1 the handle records
  * CUDA events on the caller's stream around each phase of kdfmm_tree_build and
  * kdfmm_fmm_accel.  ms (host, KDFMM_NPHASES floats, may be NULL) receives the

@@ -282,7 +282,7 @@ static kdfmm_tree_s::GraphKey graph_key_of(const kdfmm_tree_s* t, const double* 
   k.temp_cap = t->L.temp_cap; k.arena = t->L.arena; k.arena_grid = t->L.arena_grid;
   k.n_sys = t->n_sys; k.cap_sys = t->cap_sys; k.min_nleaf = t->min_nleaf;
   k.soft_kind = t->p.soft_kind; k.precision = t->p.precision; k.r_kern = t->p.r_kern;
-  k.expansion = t->p.expansion; k.walk = t->p.walk;
+  k.expansion = t->p.expansion; k.walk = t->p.walk; k.budget = t->walk_budget;
   return k;
 }
 
@@ -572,6 +572,14 @@ int kdfmm_tree_stats(kdfmm_tree t, int64_t* stats) {
   }
   hs[KDFMM_STAT_LAUNCHES] = t->launches;
   memcpy(stats, hs, KDFMM_NSTATS * sizeof(int64_t));
+  return KDFMM_OK;
+}
+
+int kdfmm_tree_set_walk_budget(kdfmm_tree t, int32_t budget) {
+  if (!t) return set_error(KDFMM_ERR_INVALID_ARG, "tree is NULL");
+  if (budget < 0 || budget > (1 << 20))
+    return set_error(KDFMM_ERR_INVALID_ARG, "walk budget %d outside [0, 2^20]", (int)budget);
+  t->walk_budget = budget;
   return KDFMM_OK;
 }
 

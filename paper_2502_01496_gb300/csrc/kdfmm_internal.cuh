@@ -191,6 +191,8 @@ struct kdfmm_tree_s {
   int64_t* host_stats = nullptr;   // pinned host mirror
   int32_t* host_counters = nullptr;
   int64_t launches = 0;            // kernels launched by this handle
+  int32_t walk_budget = 0;         // cells a walk thread visits before its leaf goes to the
+                                   // block-wide walk (0: the default)
 
   // symmetric dual-tree walk (KDFMM_WALK_DUAL): pair queues, the far and near
   // pair lists, per-cell far lists and per-cell local expansions
@@ -217,12 +219,12 @@ struct kdfmm_tree_s {
     const void *x, *m, *h;
     void *a, *phi;
     int64_t n, cap_n, cap_far, cap_near, far_cap, near_cap, seg_cap, temp_cap;
-    int32_t n_sys, cap_sys, min_nleaf, soft_kind, precision, expansion, walk, arena_grid;
+    int32_t n_sys, cap_sys, min_nleaf, soft_kind, precision, expansion, walk, arena_grid, budget;
     bool arena;
     double r_kern;
     bool operator==(const GraphKey& o) const {
       return x == o.x && m == o.m && h == o.h && a == o.a && phi == o.phi && n == o.n &&
-             expansion == o.expansion && walk == o.walk &&
+             expansion == o.expansion && walk == o.walk && budget == o.budget &&
              cap_n == o.cap_n && cap_far == o.cap_far && cap_near == o.cap_near &&
              far_cap == o.far_cap && near_cap == o.near_cap && seg_cap == o.seg_cap &&
              temp_cap == o.temp_cap && arena == o.arena && arena_grid == o.arena_grid &&

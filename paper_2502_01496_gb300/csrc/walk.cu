@@ -556,9 +556,11 @@ __global__ void __launch_bounds__(kHeavyThreads) k_walk_heavy(WalkArgs W) {
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-// Cells one thread walks before its leaf goes to the block-wide walk
-// (KDFMM_WALK_BUDGET overrides it; the lists do not depend on it).
-static int walk_budget() {
+// Cells one thread walks before its leaf goes to the block-wide walk: the
+// handle's setting (kdfmm_tree_set_walk_budget), else KDFMM_WALK_BUDGET, else
+// 4096 (the lists do not depend on it).
+static int walk_budget(const kdfmm_tree_s* t) {
+  if (t->walk_budget > 0) return t->walk_budget;
   const char* v = getenv("KDFMM_WALK_BUDGET");
   if (v != nullptr) {
     const long b = strtol(v, nullptr, 10);
@@ -643,7 +645,7 @@ static WalkArgs walk_args(kdfmm_tree_s* t) {
   W.near_off = L.near_off;
   W.maxc = t->counters + C_MAXFAR;
   W.stats = reinterpret_cast<unsigned long long*>(L.near_np);
-  W.budget = walk_budget();
+  W.budget = walk_budget(t);
   W.heavy = L.heavy;
   W.heavy_n = t->counters + C_HEAVY;
   return W;
@@ -684,7 +686,7 @@ static void walk_launch(kdfmm_tree_s* t, WalkArgs W, ListMode mode, int64_t cf, 
 static int ensure_temp(kdfmm_tree_s* t, int leaves) {
   Lists& L = t->L;
   L.arena_grid = arena_grid_for(leaves);
-  const int64_t need = (int64_t)L.arena_grid * 128 * walk_budget();
+  const int64_t need = (int64_t)L.arena_grid * 128 * walk_budget(t);
   if (L.temp_cap >= need && L.temp != nullptr) return KDFMM_OK;
   cudaFree(L.temp);
   L.temp = nullptr;

@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
     L.kdfmm_kick_drift.argtypes = [P, P, P, i64, ctypes.c_double, ctypes.c_double, P]
     L.kdfmm_tree_timing.argtypes = [P, ctypes.c_int, P]
     L.kdfmm_measure_peaks.argtypes = [P, P]
+    L.kdfmm_tree_set_walk_budget.argtypes = [P, i32]
     L.kdfmm_tree_timing.restype = i32
     L.kdfmm_last_error.restype = ctypes.c_char_p
     L.kdfmm_last_error.argtypes = []
@@ -289,6 +290,12 @@ def tree_timing(tree, enable: bool = True, read: bool = True) -> dict | None:
                                    None if ms is None else ms.ctypes.data_as(ctypes.c_void_p)),
            "tree_timing")
     return None if ms is None else {k: float(v) for k, v in zip(PHASES, ms)}
+
+
+def tree_set_walk_budget(tree, budget: int) -> None:
+    """Cells a walk thread visits before its leaf goes to the block-wide walk
+    (0: the default); see kdfmm_tree_set_walk_budget."""
+    _check(lib().kdfmm_tree_set_walk_budget(tree, int(budget)), "tree_set_walk_budget")
 
 
 def measure_peaks(stream=None) -> dict:

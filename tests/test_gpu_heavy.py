@@ -124,3 +124,43 @@ def test_naturally_heavy_leaves_262144(oracle):
     rows = np.nonzero(np.isfinite(oa[:, 0]))[0]
     ea, ep = rel_errors(ga, gphi, oa, ophi, rows)
     assert ea.max() < TOL[MIXED] and ep.max() < TOL[MIXED], (ea.max(), ep.max())
+
+
+def test_walk_budget_setting_changes_no_result():
+    """kdfmm_tree_set_walk_budget only moves leaves between the thread walk
+    and the block-wide walk: lists and forces are bit-identical for any
+    budget, on a single system and on a captured forest (whose graph is
+    captured again when the budget changes)."""
+    import torch
+    from paper_2502_01496_gb300 import native
+    ps = W.plummer(1 << 16, W.seed_for(4, 31))
+    ref_f, ref_a, ref_phi = _eval(ps, 0.5, MIXED)
+    ref_ex = ref_f.export(lists=True)
+    f = native.KdFmm(theta=0.5, eps=ps.eps, n_leaf=16, soft_kind=0, precision=MIXED)
+    x, m = _cuda(ps.x), _cuda(ps.m)
+    for budget in (3, 300, 0):
+        native.tree_set_walk_budget(f.handle, budget)
+        f.build(x, m)
+        a, phi = f.accel()
+        torch.cuda.synchronize()
+        ex = f.export(lists=True)
+        assert np.array_equal(ex.far_idx, ref_ex.far_idx) and np.array_equal(ex.near_idx, ref_ex.near_idx)
+        assert np.array_equal(a.cpu().numpy(), ref_a) and np.array_equal(phi.cpu().numpy(), ref_phi)
+    # a forest of two systems through the captured-graph path
+    sizes = np.array([5000, 20000])
+    systems = [W.plummer(int(k), W.seed_for(4, 40 + i)) for i, k in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    xs = _cuda(np.concatenate([p.x for p in systems]))
+    ms = _cuda(np.concatenate([p.m for p in systems]))
+    out = []
+    for budget in (0, 5, 0):
+        native.tree_set_walk_budget(f.handle, budget)
+        ab = torch.empty((int(off[-1]), 3), dtype=torch.float64, device="cuda")
+        for _ in range(3):                                  # eager, capture, replay
+            native.fmm_accel_batched(f.handle, xs, ms, None, off, f.params, ab, None,
+                                     theta=np.array([0.4, 0.8]), n_leaf=np.array([16, 12], dtype=np.int32))
+        torch.cuda.synchronize()
+        out.append(ab.cpu().numpy())
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    with pytest.raises(native.KdfmmError):
+        native.tree_set_walk_budget(f.handle, -1)
