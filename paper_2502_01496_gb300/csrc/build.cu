@@ -165,7 +165,7 @@ __global__ void k_chunk_map(const Seg* __restrict__ segs, const int32_t* __restr
   if (threadIdx.x == 0) counters[4] = carry;
 }
 
-// Chunk partial sums (pairwise subtree of 2048 elements) and bounding box keys.
+// Chunk partial sums (pairwise subtree of kChunk elements) and bounding box keys.
 __global__ void __launch_bounds__(kChunkThreads)
 k_chunk_reduce(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_seg,
                const int32_t* __restrict__ seg_off, const int32_t* __restrict__ counters,
@@ -202,8 +202,16 @@ k_chunk_reduce(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_s
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    Sum4 t = add4(add4(add4(ws[0], ws[1]), add4(ws[2], ws[3])),
-                  add4(add4(ws[4], ws[5]), add4(ws[6], ws[7])));
+    // perfect tree over the warps' subtrees (the top levels of the chunk's tree)
+    constexpr int kW = kChunkThreads / 32;
+    Sum4 t4[kW];
+#pragma unroll
+    for (int q = 0; q < kW; ++q) t4[q] = ws[q];
+#pragma unroll
+    for (int width = kW; width > 1; width >>= 1)
+#pragma unroll
+      for (int q = 0; q < width / 2; ++q) t4[q] = add4(t4[2 * q], t4[2 * q + 1]);
+    const Sum4 t = t4[0];
     csum[4 * b + 0] = t.m; csum[4 * b + 1] = t.x; csum[4 * b + 2] = t.y; csum[4 * b + 3] = t.z;
     for (int d = 0; d < 6; ++d) {
       long long r = wk[0][d];
@@ -1101,23 +1109,25 @@ __global__ void k_upward(Cells c, const int32_t* __restrict__ leaf_cells, const 
   const int k_n = counters[C_LEAVES];
   KD_GRID_STRIDE(k, k_n) {
   const int t = leaf_cells[k];
-  double q[6] = {0, 0, 0, 0, 0, 0}, hm = 0.0;
+  double q[6], hm = 0.0;
   {
+    // S_jk = sum m y_j y_k (9 float64 operations a particle), then
+    // Q = 3 S - tr(S) I (Eq. 7) once for the leaf
     const int f = c.first[t], cnt = c.count[t];
     const double cx = c.cx[t], cy = c.cy[t], cz = c.cz[t];
+    double S[6] = {0, 0, 0, 0, 0, 0};
     for (int j = 0; j < cnt; ++j) {
       const int64_t i = (int64_t)f + j;
       const double m = tp.m[i];
       const double y0 = tp.x[i] - cx, y1 = tp.y[i] - cy, y2 = tp.z[i] - cz;
-      const double y2s = y0 * y0 + y1 * y1 + y2 * y2;
-      q[0] += m * (3.0 * y0 * y0 - y2s);
-      q[1] += m * (3.0 * y0 * y1);
-      q[2] += m * (3.0 * y0 * y2);
-      q[3] += m * (3.0 * y1 * y1 - y2s);
-      q[4] += m * (3.0 * y1 * y2);
-      q[5] += m * (3.0 * y2 * y2 - y2s);
+      const double my0 = m * y0, my1 = m * y1, my2 = m * y2;
+      S[0] = fma(my0, y0, S[0]); S[1] = fma(my0, y1, S[1]); S[2] = fma(my0, y2, S[2]);
+      S[3] = fma(my1, y1, S[3]); S[4] = fma(my1, y2, S[4]); S[5] = fma(my2, y2, S[5]);
       hm = fmax(hm, tp.h[i]);
     }
+    const double tr = S[0] + S[3] + S[5];
+    q[0] = 3.0 * S[0] - tr; q[1] = 3.0 * S[1]; q[2] = 3.0 * S[2];
+    q[3] = 3.0 * S[3] - tr; q[4] = 3.0 * S[4]; q[5] = 3.0 * S[5] - tr;
   }
   for (int j = 0; j < 6; ++j) c.Q[6 * t + j] = q[j];
   c.hmax[t] = hm;
@@ -1132,16 +1142,19 @@ __global__ void k_upward(Cells c, const int32_t* __restrict__ leaf_cells, const 
     double qp[6] = {0, 0, 0, 0, 0, 0}, hp = 0.0;
     const int ch[2] = {c.left[p], c.right[p]};
     for (int side = 0; side < 2; ++side) {
+      // parallel-axis shift of the child's Q to the parent's centre of mass:
+      // + M (3 d d - |d|^2 I)
       const int kc = ch[side];
       const double mk = c.M[kc];
       const double d0 = c.cx[kc] - px, d1 = c.cy[kc] - py, d2 = c.cz[kc] - pz;
-      const double dd = d0 * d0 + d1 * d1 + d2 * d2;
-      qp[0] += __ldcg(&c.Q[6 * kc + 0]) + mk * (3.0 * d0 * d0 - dd);
-      qp[1] += __ldcg(&c.Q[6 * kc + 1]) + mk * (3.0 * d0 * d1);
-      qp[2] += __ldcg(&c.Q[6 * kc + 2]) + mk * (3.0 * d0 * d2);
-      qp[3] += __ldcg(&c.Q[6 * kc + 3]) + mk * (3.0 * d1 * d1 - dd);
-      qp[4] += __ldcg(&c.Q[6 * kc + 4]) + mk * (3.0 * d1 * d2);
-      qp[5] += __ldcg(&c.Q[6 * kc + 5]) + mk * (3.0 * d2 * d2 - dd);
+      const double m0 = 3.0 * mk * d0, m1 = 3.0 * mk * d1;
+      const double mdd = mk * (d0 * d0 + d1 * d1 + d2 * d2);
+      qp[0] += __ldcg(&c.Q[6 * kc + 0]) + fma(m0, d0, -mdd);
+      qp[1] += __ldcg(&c.Q[6 * kc + 1]) + m0 * d1;
+      qp[2] += __ldcg(&c.Q[6 * kc + 2]) + m0 * d2;
+      qp[3] += __ldcg(&c.Q[6 * kc + 3]) + fma(m1, d1, -mdd);
+      qp[4] += __ldcg(&c.Q[6 * kc + 4]) + m1 * d2;
+      qp[5] += __ldcg(&c.Q[6 * kc + 5]) + fma(3.0 * mk * d2, d2, -mdd);
       hp = fmax(hp, __ldcg(&c.hmax[kc]));
     }
     for (int j = 0; j < 6; ++j) c.Q[6 * p + j] = qp[j];

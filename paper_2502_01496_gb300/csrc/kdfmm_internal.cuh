@@ -14,6 +14,7 @@ namespace kdfmm {
 // ---------------------------------------------------------------------------
 constexpr int kChunk = 2048;           // phase-A reduction chunk (elements)
 constexpr int kChunkThreads = 256;     // 8 consecutive elements per thread
+static_assert(kChunk == 8 * kChunkThreads, "the chunk reduce sums 8 elements per thread");
 constexpr int kSubtreeMax = 2048;      // cells this small finish in shared memory
 constexpr int kSubtreeThreads = 256;
 constexpr int kNumStatus = 4;

@@ -24,7 +24,8 @@
 // centres (from (high, low) float pairs), so no large coordinate enters the
 // float32 arithmetic.  Each near leaf's contribution is summed in float32 and
 // folded into a (high, low) accumulator with two-sum; the long-range part is
-// added in float64 at the end.  FP64 mode uses float64 absolute positions.
+// added to the (high, low) pairs and the result converted to float64 once.
+// FP64 mode uses float64 absolute positions.
 #include <algorithm>
 #include <climits>
 
@@ -445,14 +446,18 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
   const float* C = A.lexp32 + 24 * (int64_t)k;
   float tx, ty, tz, tp_;
   l2p_tail<float>(C, xa.x, xa.y, xa.z, tx, ty, tz, tp_);
-  const double ax = (double)axh + (double)axl - ((double)C[1] + (double)C[21]) + (double)tx;
-  const double ay = (double)ayh + (double)ayl - ((double)C[2] + (double)C[22]) + (double)ty;
-  const double az = (double)azh + (double)azl - ((double)C[3] + (double)C[23]) + (double)tz;
+  // a = a_short + a_long (Eq. 3) and phi likewise, summed as (high, low)
+  // float pairs and converted to float64 once (the FP64 pipe runs at 1/64 rate)
+  df_add2(axh, axl, -C[1], -C[21]);
+  df_add2(ayh, ayl, -C[2], -C[22]);
+  df_add2(azh, azl, -C[3], -C[23]);
+  df_add2(ph_, pl, C[0], C[20]);
+  df_add(axh, axl, tx); df_add(ayh, ayl, ty); df_add(azh, azl, tz); df_add(ph_, pl, tp_);
   const int64_t ci = A.tp.idx[fa + t];
-  A.a[3 * ci + 0] = ax;
-  A.a[3 * ci + 1] = ay;
-  A.a[3 * ci + 2] = az;
-  if (A.phi) A.phi[ci] = (double)ph_ + (double)pl + ((double)C[0] + (double)C[20]) + (double)tp_;
+  A.a[3 * ci + 0] = (double)axh + (double)axl;
+  A.a[3 * ci + 1] = (double)ayh + (double)ayl;
+  A.a[3 * ci + 2] = (double)azh + (double)azl;
+  if (A.phi) A.phi[ci] = (double)ph_ + (double)pl;
   }
 }
 
