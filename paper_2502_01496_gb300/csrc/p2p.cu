@@ -139,23 +139,24 @@ __device__ __forceinline__ void pair32(float rx, float ry, float rz, float mj, c
 //   q < 1     : g/r = h^-3 (4/3 - 6/5 q^2 + 1/2 q^3),
 //               psi = h^-1 (7/5 - 2/3 q^2 + 3/10 q^4 - 1/10 q^5)
 //   1 <= q < 2: g/r = r^-3 (1 - t^4 (1 - 4/5 t + t^2/6)),  t = 2 - q
-//               psi = 1/r + h^-1 R(q), R = 8/5 - 4/3 q^2 + q^3 - 3/10 q^4 + q^5/30 - 16/15 q^-1
-//   q >= 2    : g/r = r^-3, psi = 1/r  (t clamped to 0, R switched off)
-// (the [1,2) force is the enclosed mass 1 - int_q^2 (2-u)^3 u^2 du written in t).
+//               psi = r^-1 (1 - t^5 (1/10 - t/30))
+//   q >= 2    : g/r = r^-3, psi = 1/r  (t clamped to 0)
+// The [1,2) force is the enclosed mass 1 - int_q^2 (2-u)^3 u^2 du written in
+// t; the [1,2) potential is 1/r + h^-1 R(q) with R = 8/5 - 4/3 q^2 + q^3 -
+// 3/10 q^4 + q^5/30 - 16/(15 q), and q R(q) = -t^5 (1/10 - t/30) exactly.
 __device__ __forceinline__ void m4_side(float r, float inv, float inv3, float hinv, float hinv3,
-                                        float h, float& f, float& p) {
+                                        float& f, float& p) {
   const float q = r * hinv;
   const float q2 = q * q;
   const float t = fmaxf(2.0f - q, 0.0f);
   const float t2 = t * t;
+  const float t4 = t2 * t2;
   const float g = 1.0f + t * (-0.8f + 0.16666667f * t);
-  const float f_out = inv3 * (1.0f - t2 * t2 * g);
+  const float f_out = inv3 * fmaf(-t4, g, 1.0f);
   const float f_in = hinv3 * (1.3333334f + q2 * (-1.2f + 0.5f * q));
   f = q < 1.0f ? f_in : f_out;
   const float p_in = hinv * (1.4f + q2 * (-0.6666667f + q2 * (0.3f - 0.1f * q)));
-  const float R = 1.6f + q2 * (-1.3333334f + q * (1.0f + q * (-0.3f + 0.033333335f * q))) -
-                  1.0666667f * (inv * h);
-  const float p_out = inv + (q < 2.0f ? hinv * R : 0.0f);
+  const float p_out = inv * fmaf(-t4 * t, fmaf(-0.033333335f, t, 0.1f), 1.0f);
   p = q < 1.0f ? p_in : p_out;
 }
 
@@ -168,8 +169,8 @@ __device__ __forceinline__ void m4pair32(float rx, float ry, float rz, float mj,
   const float r = r2 * inv;
   const float inv3 = inv * inv * inv;
   float fa, pa, fb, pb;
-  m4_side(r, inv, inv3, hi.x, hi.y, hi.z, fa, pa);
-  m4_side(r, inv, inv3, hj.x, hj.y, hj.z, fb, pb);
+  m4_side(r, inv, inv3, hi.x, hi.y, fa, pa);
+  m4_side(r, inv, inv3, hj.x, hj.y, fb, pb);
   const float mf = 0.5f * mj * (fa + fb);
   fx -= mf * rx; fy -= mf * ry; fz -= mf * rz;
   fp -= 0.5f * mj * (pa + pb);
@@ -202,9 +203,10 @@ __device__ __forceinline__ void near_leaf32(const P2PArgs& A, int fb, int nb, in
   for (int j = sl; j < nb; j += K) {
     if (SELF && j == t) continue;
     const float4 s = A.pf[fb + j];
-    float4 hj = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (SOFT == KDFMM_SOFT_M4) hj = A.ph[fb + j];
-    pair32<SOFT>(xs - s.x, ys - s.y, zs - s.z, s.w, hi, hj, eps2f, fx, fy, fz, fp);
+    if (SOFT == KDFMM_SOFT_M4)     // own leaf: nearly every pair is inside a support
+      m4pair32(xs - s.x, ys - s.y, zs - s.z, s.w, hi, A.ph[fb + j], fx, fy, fz, fp);
+    else
+      pair32<SOFT>(xs - s.x, ys - s.y, zs - s.z, s.w, hi, hi, eps2f, fx, fy, fz, fp);
   }
 }
 
