@@ -1175,7 +1175,8 @@ __global__ void k_derive_cells(Cells c, const int32_t* __restrict__ counters, fl
   KD_GRID_STRIDE(t, t_n) {
   const double cx = c.cx[t], cy = c.cy[t], cz = c.cz[t];
   c.walk[t] = make_float4((float)cx, (float)cy, (float)cz, (float)c.s[t]);
-  c.walk2[t] = make_float2((float)c.hmax[t], __int_as_float(c.skip[t]));
+  c.walk2[t] = make_float4((float)c.hmax[t], __int_as_float(c.skip[t]), __int_as_float(c.count[t]),
+                          0.0f);
   const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
   c.src32[4 * t + 0] = make_float4(hx, hy, hz, (float)c.M[t]);
   c.src32[4 * t + 1] = make_float4((float)(cx - (double)hx), (float)(cy - (double)hy),

@@ -82,7 +82,7 @@ struct Cells {
   double* Q;                 // 6 per cell: xx xy xz yy yz zz
   // derived views
   float4* walk;              // (com x y z, s) in float32 for the walk's filter
-  float2* walk2;             // (h_max, skip as int bits)
+  float4* walk2;             // (h_max, skip, particle count as int bits, 0)
   float4* src32;             // 4 per cell: (hi xyz, M), (lo xyz, 0), (Q xx xy xz yy), (Q yz zz, 0, 0)
   double* src64;             // 10 per cell: com xyz, M, Q[6]
   int32_t* ready;            // bottom-up arrival counters

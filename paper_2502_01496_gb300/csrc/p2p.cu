@@ -53,7 +53,7 @@ struct P2PArgs {
   const float* lexp32;
   const double* lexp64;
   const float4* walk;        // cell (com, s) float32
-  const float2* walk2;       // cell (h_max, skip)
+  const float4* walk2;       // cell (h_max, skip, count, 0)
   const int32_t* leaf_sys;   // system of each leaf
   const double* sys_eps;     // Plummer softening length of each system
   double* a;
@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
   const float4 ca = A.src32[4 * a], cal = A.src32[4 * a + 1];
   const float sa = A.walk[a].w, hmax_a = A.walk2[a].x;
   const double eps = A.sys_eps[A.leaf_sys[k]];
-  const float eps2f = (float)(eps * eps);
+  float eps2f = (float)(eps * eps);
+  asm("" : "+f"(eps2f));   // opaque: not recomputed in float64 at every pair
   float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, azh = 0.f, azl = 0.f, ph_ = 0.f, pl = 0.f;
   if (!seg) {
     float fx = 0.f, fy = 0.f, fz = 0.f, fp = 0.f;

@@ -28,7 +28,7 @@ namespace {
 
 struct WalkArgs {
   const float4* walk;
-  const float2* walk2;
+  const float4* walk2;            // (h_max, skip, count, 0)
   const double *cx, *cy, *cz, *s, *hmax;
   const int32_t* count;
   const int32_t* leaf_cells;
@@ -86,33 +86,67 @@ __device__ __forceinline__ int open_filter(float4 a, float ha, float4 b, float h
   return -1;
 }
 
-// The depth-first walk of leaf k into one thread's arena scratch: far entries
-// to far[0 ..), near entries to near[0], near[-1], ... (the scratch's other
-// end).  Returns false when the walk passes W.budget visited cells (a large
-// leaf in the sparse outskirts of a centrally condensed system opens most of
-// the tree): the leaf is then queued for k_walk_heavy, which redoes it with a
-// block.
-__device__ __forceinline__ bool walk_leaf(const WalkArgs& W, int k, int32_t* far, int32_t* near,
+// The depth-first walk of leaf k (`valid` false: no leaf, the lane only
+// keeps the warp company), emitting far entries with far(nf, cell) and near
+// entries with near(nn, cell).  Must be called by all 32 lanes of the warp.
+// Returns false for an invalid lane and for a leaf whose walk passes W.budget
+// visited cells (a large leaf in the sparse outskirts of a centrally
+// condensed system opens most of the tree): that leaf is queued for
+// k_walk_heavy, which redoes it with a block.  Within the budget a walk emits
+// at most W.budget entries.
+//
+// The cell's record is loaded first in a step, ahead of the budget test, so
+// that its latency overlaps the test (loads behind that branch made the walk
+// 8 to 13 % slower).  SYNC makes the loop warp-synchronous (a vote at its
+// head), so the lanes reconverge at every step and a record load is one
+// instruction for all walking lanes: 3 % faster on the slot-mode walk of a
+// binary polytrope, 4 % slower on the arena walk of a Plummer sphere, whose
+// lanes' walks differ more in length (the slot walk syncs, the arena walk
+// runs free).
+// The float32 copies of theta and R_kern and the theta = 0 flag go through
+// an empty asm, which makes them opaque values: otherwise the compiler, short
+// of registers, recomputes them from the float64 values at every step, and on
+// this part a float64 conversion or comparison occupies the float64 pipe 64
+// cycles a warp instruction (two such instructions a step kept it 43 % busy).
+template <bool SYNC, class Far, class Near>
+__device__ __forceinline__ bool walk_leaf(const WalkArgs& W, int k, bool valid, Far far, Near near,
                                           int& nf, int& nn, long long& np, int& nex) {
-  const int a = W.leaf_cells[k];
-  const float4 wa = W.walk[a];
-  const float ha = W.walk2[a].x;
-  const double ax = W.cx[a], ay = W.cy[a], az = W.cz[a], sa = W.s[a], ha64 = W.hmax[a];
+  const unsigned full = 0xffffffffu;
+  float4 wa = make_float4(0.f, 0.f, 0.f, 0.f);
+  float ha = 0.f;
+  double ax = 0., ay = 0., az = 0., sa = 0., ha64 = 0., theta = 0.;
+  int i = 0, i_end = 0;
+  if (valid) {
+    const int a = W.leaf_cells[k];
+    wa = W.walk[a];
+    ha = W.walk2[a].x;
+    ax = W.cx[a]; ay = W.cy[a]; az = W.cz[a]; sa = W.s[a]; ha64 = W.hmax[a];
+    const int sys = W.leaf_sys[k];
+    theta = W.sys_theta[sys];
+    i = W.sys_root[sys];                // the walk stays inside the leaf's own tree
+    i_end = W.sys_root[sys + 1];
+  }
   const float bound = *W.com_bound;
-  const int sys = W.leaf_sys[k];
-  const double theta = W.sys_theta[sys];
-  const int i_end = W.sys_root[sys + 1];
-  const float thf = (float)theta, rkf = (float)W.r_kern;
-  const bool always = theta == 0.0;
-  int i = W.sys_root[sys];              // the walk stays inside the leaf's own tree
+  float thf = (float)theta, rkf = (float)W.r_kern;
+  int always = theta == 0.0;
+  asm("" : "+f"(thf), "+f"(rkf), "+r"(always));
+  bool ok = valid;
   int visits = 0;
-  while (i < i_end) {
-    if (++visits > W.budget) {
-      W.heavy[atomicAdd(W.heavy_n, 1)] = k;
-      return false;
+  for (;;) {
+    if (SYNC) {
+      if (!__any_sync(full, i < i_end)) break;
+      if (i >= i_end) continue;
+    } else if (i >= i_end) {
+      break;
     }
     const float4 wb = W.walk[i];
-    const float2 w2 = W.walk2[i];
+    const float4 w2 = W.walk2[i];
+    if (++visits > W.budget) {
+      W.heavy[atomicAdd(W.heavy_n, 1)] = k;
+      ok = false;
+      i_end = 0;
+      continue;
+    }
     const int skip = __float_as_int(w2.y);
     int o = always ? 1 : open_filter(wa, ha, wb, w2.x, thf, rkf, bound);
     if (o < 0) {
@@ -122,18 +156,18 @@ __device__ __forceinline__ bool walk_leaf(const WalkArgs& W, int k, int32_t* far
     }
     if (o) {
       if (skip == i + 1) {                    // opened leaf: short range
-        near[-nn] = i;
-        np += W.count[i];
+        near(nn, i);
+        np += __float_as_int(w2.z);
         ++nn;
       }
       i = i + 1;
     } else {                                  // closed: long range, skip its subtree
-      far[nf] = i;
+      far(nf, i);
       ++nf;
       i = skip;
     }
   }
-  return true;
+  return ok;
 }
 
 __device__ __forceinline__ void walk_stats(const WalkArgs& W, int k, int nf, int nn, long long np,
@@ -149,10 +183,8 @@ __device__ __forceinline__ void walk_stats(const WalkArgs& W, int k, int nf, int
 // the leaf (entries beyond the capacity are counted, not stored; the host
 // then grows the slots and walks again, or changes mode).  Two-pass mode: the
 // counts of a previous pass, scanned, give each leaf's start.  A leaf whose
-// walk passes W.budget visited cells is queued for k_walk_heavy.  (The walk
-// is written out here, with the offsets either computed or given, rather than
-// shared with walk_leaf: this form measured 7 % faster in ncu kernel time on
-// the slot-mode benchmark walk.)
+// walk passes W.budget visited cells is queued for k_walk_heavy, which writes
+// its lists and counts.
 __global__ void __launch_bounds__(128, 10) k_walk(WalkArgs W) {
   // the grid covers slot_leaves leaves; more leaves than slots is flagged and
   // the evaluation is redone by the host
@@ -160,73 +192,33 @@ __global__ void __launch_bounds__(128, 10) k_walk(WalkArgs W) {
   if (!W.exact && nleaves > W.slot_leaves && blockIdx.x == 0 && threadIdx.x == 0)
     atomicOr(W.status, ST_LISTS);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nleaves || (!W.exact && k >= W.slot_leaves)) return;
-  {
-  const int a = W.leaf_cells[k];
-  const float4 wa = W.walk[a];
-  const float ha = W.walk2[a].x;
-  const double ax = W.cx[a], ay = W.cy[a], az = W.cz[a], sa = W.s[a], ha64 = W.hmax[a];
-  const float bound = *W.com_bound;
-  const int sys = W.leaf_sys[k];
-  const double theta = W.sys_theta[sys];
-  const int i_end = W.sys_root[sys + 1];
-  const float thf = (float)theta, rkf = (float)W.r_kern;
-  const bool always = theta == 0.0;
-  int64_t fo, no;
-  if (W.exact) {
+  if (k - (int)(threadIdx.x & 31) >= nleaves) return;       // the whole warp is past the leaves
+  const bool valid = k < nleaves && (W.exact || k < W.slot_leaves);
+  int64_t fo = 0, no = 0;
+  if (valid && W.exact) {
     fo = W.far_off[k];
     no = W.near_off[k];
-  } else {
+  } else if (valid) {
     fo = (int64_t)k * W.cap_far;
     no = (int64_t)k * W.cap_near;
     W.far_off[k] = fo;
     W.near_off[k] = no;
   }
-  int32_t* far = W.far_idx + fo;
-  int32_t* near = W.near_idx + no;
+  int32_t* const far_l = W.far_idx + fo;
+  int32_t* const near_l = W.near_idx + no;
   const int64_t cap_far = W.exact ? INT64_MAX : W.cap_far;
   const int64_t cap_near = W.exact ? INT64_MAX : W.cap_near;
   int nf = 0, nn = 0, nex = 0;
   long long np = 0;
-  int i = W.sys_root[sys];              // the walk stays inside the leaf's own tree
-  int visits = 0;
-  while (i < i_end) {
-    if (++visits > W.budget) {
-      W.heavy[atomicAdd(W.heavy_n, 1)] = k;
-      return;
-    }
-    const float4 wb = W.walk[i];
-    const float2 w2 = W.walk2[i];
-    const int skip = __float_as_int(w2.y);
-    int o = always ? 1 : open_filter(wa, ha, wb, w2.x, thf, rkf, bound);
-    if (o < 0) {
-      o = open_exact(ax, ay, az, sa, ha64, W.cx[i], W.cy[i], W.cz[i], W.s[i], W.hmax[i], theta,
-                     W.r_kern);
-      ++nex;
-    }
-    if (o) {
-      if (skip == i + 1) {                    // opened leaf: short range
-        if (nn < cap_near) near[nn] = i;
-        np += W.count[i];
-        ++nn;
-      }
-      i = i + 1;
-    } else {                                  // closed: long range, skip its subtree
-      if (nf < cap_far) far[nf] = i;
-      ++nf;
-      i = skip;
-    }
-  }
+  if (!walk_leaf<true>(
+          W, k, valid, [&](int e, int c) { if (e < cap_far) far_l[e] = c; },
+          [&](int e, int c) { if (e < cap_near) near_l[e] = c; }, nf, nn, np, nex))
+    return;
   W.far_cnt[k] = nf;
   W.near_cnt[k] = nn;
-  atomicMax(&W.maxc[0], nf);
-  atomicMax(&W.maxc[1], nn);
-  const long long na = W.count[a];
-  atomicAdd(&W.stats[0], (unsigned long long)(na * np - na));
+  walk_stats(W, k, nf, nn, np, nex);
   atomicAdd(&W.stats[2], (unsigned long long)nf);
   atomicAdd(&W.stats[3], (unsigned long long)nn);
-  if (nex) atomicAdd(&W.stats[1], (unsigned long long)nex);
-  }
 }
 
 // Copies the warp's 32 lists (lane l's list: n entries at src(l), starting at
@@ -286,9 +278,10 @@ __global__ void __launch_bounds__(128, 10) k_walk_arena(WalkArgs W) {
     const int k = (int)kb + lane;
     int nf = 0, nn = 0, nex = 0;
     long long np = 0;
-    bool ok = false;
-    if (k < nleaves)
-      ok = walk_leaf(W, k, temp, temp + (B - 1), nf, nn, np, nex);
+    int32_t* const near_l = temp + (B - 1);
+    const bool ok = walk_leaf<false>(
+        W, k, k < nleaves, [&](int e, int c) { temp[e] = c; }, [&](int e, int c) { near_l[-e] = c; },
+        nf, nn, np, nex);
     if (!ok) nf = nn = 0;
     int fi = nf, ni = nn;
 #pragma unroll
@@ -429,8 +422,9 @@ __global__ void __launch_bounds__(kHeavyThreads) k_walk_heavy(WalkArgs W) {
     const int sys = W.leaf_sys[k];
     const double theta = W.sys_theta[sys];
     const int i0 = W.sys_root[sys], i_end = W.sys_root[sys + 1];
-    const float thf = (float)theta, rkf = (float)W.r_kern;
-    const bool always = theta == 0.0;
+    float thf = (float)theta, rkf = (float)W.r_kern;
+    int always = theta == 0.0;
+    asm("" : "+f"(thf), "+f"(rkf), "+r"(always));   // opaque: see walk_leaf
     int64_t fo = W.exact ? W.far_off[k] : (int64_t)k * W.cap_far;
     int64_t no = W.exact ? W.near_off[k] : (int64_t)k * W.cap_near;
     int64_t cap_far = W.exact ? INT64_MAX : W.cap_far;
@@ -459,7 +453,7 @@ __global__ void __launch_bounds__(kHeavyThreads) k_walk_heavy(WalkArgs W) {
         ex[j] = false;
         if (c < i_end) {
           const float4 wb = W.walk[c];
-          const float2 w2 = W.walk2[c];
+          const float4 w2 = W.walk2[c];
           sk[j] = __float_as_int(w2.y);
           o[j] = always ? 1 : open_filter(wa, ha, wb, w2.x, thf, rkf, bound);
           if (o[j] < 0) {
