@@ -97,7 +97,9 @@ typedef struct {
 #define KDFMM_STAT_NFALLBACK 7    /* degenerate cuts split by position */
 #define KDFMM_STAT_NEXACT 8       /* opening decisions settled in float64 */
 #define KDFMM_STAT_LAUNCHES 9     /* kernels launched since the handle was created */
-#define KDFMM_NSTATS 10
+#define KDFMM_STAT_NHEAVY 10      /* leaves whose walk passed the walk budget and was redone
+                                     block-wide (leaf walk; 0 for the dual walk) */
+#define KDFMM_NSTATS 11
 
 /* Phases timed by kdfmm_tree_timing (milliseconds of the most recent call). */
 #define KDFMM_PHASE_BUILD 0       /* kdfmm_tree_build: tree + moments */

@@ -248,7 +248,7 @@ static int build_common(kdfmm_tree_s* t, const double* x, const double* m, const
   hs[KDFMM_STAT_DEPTH] = t->depth;
   hs[KDFMM_STAT_NFAR] = hs[KDFMM_STAT_NNEAR] = hs[KDFMM_STAT_NP2P] = 0;
   hs[KDFMM_STAT_NFALLBACK] = t->nfallback;
-  hs[KDFMM_STAT_NEXACT] = 0;
+  hs[KDFMM_STAT_NEXACT] = hs[KDFMM_STAT_NHEAVY] = 0;
   return KDFMM_OK;
 }
 
@@ -569,6 +569,12 @@ int kdfmm_tree_stats(kdfmm_tree t, int64_t* stats) {
     if (rc) return rc;
     hs[KDFMM_STAT_NP2P] = dev[0];
     hs[KDFMM_STAT_NEXACT] = dev[1];
+    int32_t heavy = 0;
+    if (t->p.walk == KDFMM_WALK_LEAF &&
+        (rc = check_cuda(cudaMemcpy(&heavy, t->counters + C_HEAVY, sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost), "stats copy")))
+      return rc;
+    hs[KDFMM_STAT_NHEAVY] = heavy;
   }
   hs[KDFMM_STAT_LAUNCHES] = t->launches;
   memcpy(stats, hs, KDFMM_NSTATS * sizeof(int64_t));

@@ -31,7 +31,7 @@ EXPANSION_PHANTOM, EXPANSION_STANDARD = 0, 1
 WALK_LEAF, WALK_DUAL = 0, 1
 MAX_LEAF = 32
 STAT_NAMES = ("n", "ncells", "nleaves", "depth", "nfar", "nnear", "np2p", "nfallback", "nexact",
-              "launches")
+              "launches", "nheavy")
 PHASES = ("build", "walk", "m2l", "p2p")
 
 

@@ -87,6 +87,38 @@ def test_block_walk_forest(oracle, monkeypatch):
 
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_block_walk_in_arena_scratch(oracle, monkeypatch, prec):
+    """Arena mode: a block-wide walk writes its leaf's lists into the block's
+    slice of the (idle) thread-walk scratch and copies them to reserved room,
+    in one pass.  Sizes: 2^15 particles, about 2900 leaves, so the arena grid
+    has 23 blocks of 128 threads and a budget of 1000 gives slices of
+    2944 * 1000 / (2 * 152 SMs) = 9684 entries, more than the system's ~5800
+    cells; at theta = 0.5 the mean walk is longer than 1000 cells, so many leaves
+    are handed on.  Lists, statistics and force bits equal the thread walk's."""
+    ps = W.plummer(1 << 15, W.seed_for(0, 98))
+    monkeypatch.setenv("KDFMM_LIST_MODE", "exact")
+    monkeypatch.setenv("KDFMM_WALK_BUDGET", "30000")       # every leaf walks in its thread
+    f0, a0, p0 = _eval(ps, 0.5, prec)
+    ex0, st0 = f0.export(lists=True), f0.stats()
+    assert st0["nheavy"] == 0, st0
+    monkeypatch.setenv("KDFMM_WALK_BUDGET", "1000")
+    f1, a1, p1 = _eval(ps, 0.5, prec)
+    ex1, st1 = f1.export(lists=True), f1.stats()
+    assert st1["nheavy"] > st1["nleaves"] // 10, st1
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    threads = -(-st1["nleaves"] // 128) * 128              # the arena grid (one round)
+    assert st1["ncells"] <= threads * 1000 // (2 * sms), st1   # the slice holds the system
+    for name in ("far_off", "far_idx", "near_off", "near_idx"):
+        assert np.array_equal(getattr(ex0, name), getattr(ex1, name)), name
+    for key in ("nfar", "nnear", "np2p", "nexact"):
+        assert st0[key] == st1[key], (key, st0[key], st1[key])
+    assert np.array_equal(a0, a1) and np.array_equal(p0, p1)
+    T = oracle.Tree(ps.x, ps.m, None, theta=0.5, n_leaf=16, soft_kind=0, eps=ps.eps)
+    assert_lists_bit_exact({"ex": ex1}, {"lists": T.walk()})
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_split_near_lists_against_oracle(oracle, prec):
     """Plummer 16384 at theta = 0.5: dozens of near lists span several
     segments.  Forces match the oracle; two evaluations give identical bits."""

@@ -80,3 +80,16 @@ def test_measure_peaks_rejects_null_output_without_a_gpu(libpath):
     from paper_2502_01496_gb300 import native
     assert native.lib().kdfmm_measure_peaks(None, None) == -1
     assert "NULL" in native.last_error()
+
+
+def test_stat_and_phase_names_match_header():
+    """The binding names one statistic per KDFMM_STAT_* index (in index
+    order, KDFMM_NSTATS of them) and one phase per KDFMM_PHASE_*."""
+    from paper_2502_01496_gb300 import native
+    src = open(os.path.join(ROOT, "include", "kdfmm.h")).read()
+    stats = dict((k, int(v)) for k, v in re.findall(r"#define KDFMM_STAT_([A-Z0-9_]+)\s+(\d+)", src))
+    nstats = int(re.search(r"#define KDFMM_NSTATS\s+(\d+)", src).group(1))
+    assert nstats == len(native.STAT_NAMES) == len(stats)
+    assert [k.lower() for k, _ in sorted(stats.items(), key=lambda kv: kv[1])] == list(native.STAT_NAMES)
+    phases = re.findall(r"#define KDFMM_PHASE_([A-Z0-9_]+)\s+(\d+)", src)
+    assert [k.lower() for k, _ in sorted(phases, key=lambda kv: int(kv[1]))] == list(native.PHASES)
