@@ -360,7 +360,10 @@ static int graph_replay(kdfmm_tree_s* t, cudaStream_t s) {
   t->built = t->evaluated = t->lists_frozen = false;
   if (st & ST_NONFINITE)
     return set_error(KDFMM_ERR_NONFINITE, "non-finite position or non-positive mass / h");
+  // more leaves than the captured launches cover (M2L and P2P stop at
+  // graph_leaves) is redone eagerly too
   if ((st & (ST_UNFINISHED | ST_LISTS | ST_CAPACITY | ST_INTERNAL)) ||
+      hc[C_LEAVES] > t->graph_leaves ||
       (!t->L.arena && (hc[C_MAXFAR] > t->L.cap_far || hc[C_MAXNEAR] > t->L.cap_near)))
     return 1;
   t->ncells = hc[C_CELLS];

@@ -352,8 +352,10 @@ __global__ void __launch_bounds__(kP2PWarps * 32, 6) k_p2p_mixed(P2PArgs A) {
         p.x += o.x; p.y += o.y; p.z += o.z;
         bool need = false;
         if (M4 && v) {
-          const float d = sqrtf(p.x * p.x + p.y * p.y + p.z * p.z);
-          need = d - sa < 2.0f * fmaxf(hmax_a, hv[r].z) * 1.0001f + 1e-20f;
+          // d - s_a < X  <=>  d^2 < (s_a + X)^2 (both sides >= 0)
+          const float d2 = p.x * p.x + p.y * p.y + p.z * p.z;
+          const float reach = sa + 2.0f * fmaxf(hmax_a, hv[r].z) * 1.0001f + 1e-20f;
+          need = d2 < reach * reach;
         }
         const unsigned vm = __ballot_sync(full, v), nm = __ballot_sync(full, v && need);
         if (v) {

@@ -222,35 +222,37 @@ __global__ void __launch_bounds__(128, 10) k_walk(WalkArgs W) {
   atomicAdd(&W.stats[3], (unsigned long long)nn);
 }
 
-// Copies the warp's 32 lists (lane l's list: n entries at src(l), starting at
-// prefix pre[l] of the warp's reserved room dst) with the entries spread
-// evenly over the lanes: entry g belongs to the last list whose prefix is
-// <= g; kCopyBatch independent loads per lane are in flight before storing.
+// Copies n entries of a list from a thread's scratch (DOWN: stored backwards
+// from src) to dst, by the 32 lanes of a warp: coalesced, kCopyBatch loads a
+// lane in flight before the stores (the copy is latency-bound otherwise).
 constexpr int kCopyBatch = 8;
 template <bool DOWN>
-__device__ __forceinline__ void warp_copy(const int32_t* __restrict__ temp, int64_t tid0, int B,
-                                          const int* pre, int total, int32_t* __restrict__ dst) {
-  const int lane = threadIdx.x & 31;
-  for (int g0 = 0; g0 < total; g0 += 32 * kCopyBatch) {
+__device__ __forceinline__ void warp_copy_list(const int32_t* __restrict__ src, int n,
+                                               int32_t* __restrict__ dst, int lane) {
+  for (int e0 = 0; e0 < n; e0 += 32 * kCopyBatch) {
     int32_t v[kCopyBatch];
 #pragma unroll
     for (int u = 0; u < kCopyBatch; ++u) {
-      const int g = g0 + 32 * u + lane;
-      v[u] = 0;
-      if (g < total) {
-        int l = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1)
-          if (pre[l + step] <= g) l += step;
-        const int e = g - pre[l];
-        v[u] = temp[(tid0 + l) * B + (DOWN ? B - 1 - e : e)];
-      }
+      const int e = e0 + 32 * u + lane;
+      v[u] = e < n ? src[DOWN ? -e : e] : 0;
     }
 #pragma unroll
     for (int u = 0; u < kCopyBatch; ++u) {
-      const int g = g0 + 32 * u + lane;
-      if (g < total) dst[g] = v[u];
+      const int e = e0 + 32 * u + lane;
+      if (e < n) dst[e] = v[u];
     }
+  }
+}
+
+// Copies the warp's 32 lists (lane l's list: pre[l + 1] - pre[l] entries of
+// thread tid0 + l's scratch, to dst + pre[l]) list by list.
+template <bool DOWN>
+__device__ __forceinline__ void warp_copy(const int32_t* __restrict__ temp, int64_t tid0, int B,
+                                          const int* pre, int32_t* __restrict__ dst) {
+  const int lane = threadIdx.x & 31;
+  for (int l = 0; l < 32; ++l) {
+    const int32_t* src = temp + (tid0 + l) * B + (DOWN ? B - 1 : 0);
+    warp_copy_list<DOWN>(src, pre[l + 1] - pre[l], dst + pre[l], lane);
   }
 }
 
@@ -262,6 +264,7 @@ __device__ __forceinline__ void warp_copy(const int32_t* __restrict__ temp, int6
 // lists with one atomic per list kind on the running totals (stats[2],
 // stats[3]) and copies them there, coalesced.  Totals beyond the buffers
 // flag ST_LISTS and store nothing (counts 0); the host grows and walks again.
+template <bool SYNC>
 __global__ void __launch_bounds__(128, 10) k_walk_arena(WalkArgs W) {
   __shared__ int s_pre[4][2][33];         // per warp: exclusive prefixes of the far and near counts
   const unsigned full = 0xffffffffu;
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(128, 10) k_walk_arena(WalkArgs W) {
     int nf = 0, nn = 0, nex = 0;
     long long np = 0;
     int32_t* const near_l = temp + (B - 1);
-    const bool ok = walk_leaf<false>(
+    const bool ok = walk_leaf<SYNC>(
         W, k, k < nleaves, [&](int e, int c) { temp[e] = c; }, [&](int e, int c) { near_l[-e] = c; },
         nf, nn, np, nex);
     if (!ok) nf = nn = 0;
@@ -318,8 +321,8 @@ __global__ void __launch_bounds__(128, 10) k_walk_arena(WalkArgs W) {
     if (lane == 31) { pf[32] = fi; pn[32] = ni; }
     __syncwarp();
     if (fits && !deferred) {
-      warp_copy<false>(W.temp, tid0, B, pf, ftot, W.far_idx + fb);
-      warp_copy<true>(W.temp, tid0, B, pn, ntot, W.near_idx + nb);
+      warp_copy<false>(W.temp, tid0, B, pf, W.far_idx + fb);
+      warp_copy<true>(W.temp, tid0, B, pn, W.near_idx + nb);
     }
     __syncwarp();
   }
@@ -336,11 +339,8 @@ __global__ void k_arena_copy(WalkArgs W, int64_t walk_threads) {
   for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < nleaves;
        k += (int)((gridDim.x * blockDim.x) >> 5)) {
     const int32_t* src = W.temp + (int64_t)k * B;
-    const int nf = W.far_cnt[k], nn = W.near_cnt[k];
-    int32_t* far = W.far_idx + W.far_off[k];
-    int32_t* near = W.near_idx + W.near_off[k];
-    for (int e = lane; e < nf; e += 32) far[e] = src[e];
-    for (int e = lane; e < nn; e += 32) near[e] = src[B - 1 - e];
+    warp_copy_list<false>(src, W.far_cnt[k], W.far_idx + W.far_off[k], lane);
+    warp_copy_list<true>(src + (B - 1), W.near_cnt[k], W.near_idx + W.near_off[k], lane);
   }
 }
 
@@ -634,7 +634,7 @@ static int arena_grid_for(int leaves) {
   static int per_sm = 0;
   const int sms = sm_count();
   if (per_sm == 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_arena, 128, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_arena<true>, 128, 0) != cudaSuccess ||
         per_sm < 1) {
       cudaGetLastError();
       per_sm = 1;
@@ -693,7 +693,15 @@ static void walk_launch(kdfmm_tree_s* t, WalkArgs W, ListMode mode, int64_t cf, 
   cudaMemsetAsync(t->counters + C_MAXFAR, 0, 2 * sizeof(int32_t), s);
   cudaMemsetAsync(t->counters + C_HEAVY, 0, sizeof(int32_t), s);
   if (arena) {
-    k_walk_arena<<<L.arena_grid, 128, 0, s>>>(W);
+    // one round (no more leaves than threads): the walk is latency-bound and
+    // its lanes run free; several rounds fill the GPU and the synchronous loop
+    // wins (3 % slower on a Plummer sphere of 2^20, 9 % faster on 256
+    // Plummer systems).  The host's leaf count picks the form; the kernel
+    // handles any count.
+    if (slot_leaves <= (int64_t)L.arena_grid * 128)
+      k_walk_arena<false><<<L.arena_grid, 128, 0, s>>>(W);
+    else
+      k_walk_arena<true><<<L.arena_grid, 128, 0, s>>>(W);
     k_arena_copy<<<grid_blocks(), 256, 0, s>>>(W, (int64_t)L.arena_grid * 128);
     t->launches += 1;
   } else {
