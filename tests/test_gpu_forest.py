@@ -234,3 +234,46 @@ def test_captured_graph_replays_the_eager_evaluation(monkeypatch, prec, list_mod
         st = f.stats()
         for key in ("ncells", "nleaves", "depth", "nfar", "nnear", "np2p"):
             assert st[key] == rst[key], (key, st[key], rst[key])
+
+
+@pytest.mark.parametrize("list_mode", ["slots", "arena"])
+def test_replay_with_more_leaves_than_captured_is_redone(monkeypatch, list_mode):
+    """A graph captured on a jittered 32^3 lattice (cuts through the centre of
+    mass halve it exactly: 2048 leaves of 16, so the graph covers 2048 * 1.25
+    + 64 = 2624) and replayed on the same buffers holding a Plummer sphere of
+    the same size (2914 leaves): the walk, M2L and P2P launches of the graph
+    stop at 2624 leaves, so the replay must be redone eagerly, with the bits
+    of a handle that never used a graph."""
+    import torch
+    from paper_2502_01496_gb300 import native
+    if list_mode == "arena":
+        monkeypatch.setenv("KDFMM_LIST_MODE", "exact")
+    g1 = np.arange(32, dtype=np.float64) / 32.0
+    X, Y, Z = np.meshgrid(g1, g1, g1, indexing="ij")
+    lattice = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    lattice += np.random.default_rng(3).uniform(-1e-4, 1e-4, lattice.shape)
+    sphere = W.plummer(32768, W.seed_for(0, 98))
+    n = 32768
+    off = np.array([0, n], dtype=np.int64)
+    x, m = _cuda(lattice), _cuda(np.full(n, 1.0 / n))
+    a = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    phi = torch.empty(n, dtype=torch.float64, device="cuda")
+    theta, n_leaf = np.array([0.5]), np.array([16], dtype=np.int32)
+    f = native.KdFmm(theta=0.5, eps=0.01, n_leaf=16, soft_kind=0, precision=MIXED)
+    for _ in range(2):                                 # eager + capture, then a replay
+        _batched(f, x, m, off, theta, n_leaf, a, phi)
+    torch.cuda.synchronize()
+    assert f.stats()["nleaves"] == 2048
+    x.copy_(_cuda(sphere.x))                           # same buffers, another tree
+    _batched(f, x, m, off, theta, n_leaf, a, phi)
+    torch.cuda.synchronize()
+    monkeypatch.setenv("KDFMM_GRAPH", "0")
+    g = native.KdFmm(theta=0.5, eps=0.01, n_leaf=16, soft_kind=0, precision=MIXED)
+    ar, pr = torch.empty_like(a), torch.empty_like(phi)
+    _batched(g, x, m, off, theta, n_leaf, ar, pr)
+    torch.cuda.synchronize()
+    st, rst = f.stats(), g.stats()
+    assert rst["nleaves"] > 2624, rst
+    for key in ("ncells", "nleaves", "nfar", "nnear", "np2p"):
+        assert st[key] == rst[key], (key, st[key], rst[key])
+    assert torch.equal(a, ar) and torch.equal(phi, pr)
