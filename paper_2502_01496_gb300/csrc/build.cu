@@ -177,19 +177,18 @@ k_chunk_reduce(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_s
   const int rel0 = (b - seg_off[s]) * kChunk;
   const int cnt = g.count - rel0;               // valid elements from the chunk start
   const int64_t base = (int64_t)g.first + rel0;
+  // the bounding-box keys come with the same loads (get runs once per element)
+  long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
   auto get = [&](int k) {
     int64_t i = base + k;
-    return elem4(p.m[i], p.x[i], p.y[i], p.z[i]);
-  };
-  Sum4 v = block_tree<3>(8 * threadIdx.x, cnt, get);
-  long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
-  for (int k = threadIdx.x; k < kChunk && k < cnt; k += kChunkThreads) {
-    int64_t i = base + k;
-    long long kx = dkey(p.x[i]), ky = dkey(p.y[i]), kz = dkey(p.z[i]);
+    const double x = p.x[i], y = p.y[i], z = p.z[i];
+    const long long kx = dkey(x), ky = dkey(y), kz = dkey(z);
     lo[0] = min(lo[0], kx); hi[0] = max(hi[0], kx);
     lo[1] = min(lo[1], ky); hi[1] = max(hi[1], ky);
     lo[2] = min(lo[2], kz); hi[2] = max(hi[2], kz);
-  }
+    return elem4(p.m[i], x, y, z);
+  };
+  Sum4 v = block_tree<3>(8 * threadIdx.x, cnt, get);
   v = warp_tree4(v);
 #pragma unroll
   for (int d = 0; d < 3; ++d) { lo[d] = warp_min_ll(lo[d]); hi[d] = warp_max_ll(hi[d]); }
@@ -304,7 +303,10 @@ k_chunk_count(const Seg* __restrict__ segs, const int32_t* __restrict__ chunk_se
               cz = trunc_to_float(tmp.cz[g.cell]);
   int nl = 0;
   float s2 = 0.0f;
-  for (int k = threadIdx.x; k < cnt; k += kChunkThreads) {
+#pragma unroll
+  for (int pass = 0; pass < kChunk / kChunkThreads; ++pass) {   // all loads in flight
+    const int k = pass * kChunkThreads + threadIdx.x;
+    if (k >= cnt) continue;
     int64_t i = base + k;
     const double px = p.x[i], py = p.y[i], pz = p.z[i];
     const double a = axis == 0 ? px : (axis == 1 ? py : pz);
