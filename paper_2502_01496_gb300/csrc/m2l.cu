@@ -204,8 +204,14 @@ __global__ void __launch_bounds__(128) k_m2l_mixed(M2LArgs A) {
 #pragma unroll
   for (int j = 0; j < 4; ++j) lo[j] = 0.0f;
   const int64_t off = A.far_off[k], nf = min((int64_t)A.far_cnt[k], A.cap_far);
+  // the next far cell's index is loaded an iteration ahead, so that each
+  // iteration waits on one L2 round trip (the moments) instead of two (6 % off
+  // the kernel; loading the next moments ahead too cost more registers than
+  // it saved)
+  int bn = lane < nf ? A.far_idx[off + lane] : 0;
   for (int64_t e = lane; e < nf; e += 32) {
-    const int b = A.far_idx[off + e];
+    const int b = bn;
+    if (e + 32 < nf) bn = A.far_idx[off + e + 32];
     const float4 b0 = A.src32[4 * b], b1 = A.src32[4 * b + 1], b2 = A.src32[4 * b + 2],
                  b3 = A.src32[4 * b + 3];
     // R = com_alpha - com_beta as (high, low) from the (high, low) centres
