@@ -308,6 +308,16 @@ def whole_job_rate(n_per_rank: int, steps: int, max_total_ms: float, world: int)
     return world * n_per_rank * steps / (max_total_ms / 1e3) / 1e6
 
 
+def settle():
+    """Frees what earlier legs left (handles in reference cycles, cached
+    blocks) and waits for the device, so that no deferred free -- a
+    synchronising cudaFree of gigabytes -- lands inside a timed region."""
+    import gc
+    import torch
+    gc.collect()
+    torch.cuda.synchronize()
+
+
 def run_batched(args, dev, flush):
     """The batch of 256 independent Plummer systems (N log-uniform in
     [2048, 262144], theta uniform in [0.3, 1], eps 0.01, mixed precision) as one
@@ -316,6 +326,7 @@ def run_batched(args, dev, flush):
     tunes leaf sizes per (theta, N) bin and the walk budget in place on this
     batch (its time is reported, outside the timed region); the defaults (16
     everywhere, library budget) are timed for comparison."""
+    settle()
     import numpy as np
     import torch
     from paper_2502_01496_gb300 import autotune, native
@@ -370,6 +381,7 @@ def run_large(args, dev, flush):
     cube and half in 64 Gaussian clumps (sigma 0.01), masses log-uniform over a
     decade, eps 1e-3, theta 0.5, leaves of at most 32, mixed precision; the
     same step as the headline (build + evaluation + total momentum)."""
+    settle()
     import statistics
     import torch
     from paper_2502_01496_gb300 import native
@@ -421,6 +433,7 @@ def run_variants(args, ps, x, m, h, flush):
     with Eq. 6 (the headline), the symmetric dual-tree walk, and the standard
     p = 3 expansion -- time per evaluation and the relative total force
     |sum m a| / sum m |a| that the leaf-only walk leaves (Sec. 4)."""
+    settle()
     import torch
     from paper_2502_01496_gb300 import native
     out = {}
