@@ -161,6 +161,13 @@ def test_invalid_arguments_return_status_codes():
     rc = L.kdfmm_tree_build(h, xh.ctypes.data_as(native.ctypes.c_void_p), native._ptr(m), None, 100,
                             native.ctypes.byref(native.make_params()), None)
     assert rc == -1
+    # empty, negative and oversized particle counts are refused before any kernel runs
+    for n_bad in (0, -5, (1 << 30) + 1):
+        rc = L.kdfmm_tree_build(h, native._ptr(x), native._ptr(m), None, n_bad,
+                                native.ctypes.byref(native.make_params()), None)
+        assert rc == -1 and "n must lie" in native.last_error(), (n_bad, native.last_error())
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
+    assert L.kdfmm_total_momentum(native._ptr(m), native._ptr(x), 0, native._ptr(out), None) == -1
     native.tree_destroy(h)
     # the handle still works after the errors
     f.build(x, m)
