@@ -264,6 +264,8 @@ __device__ __forceinline__ void warp_copy(const int32_t* __restrict__ temp, int6
 // lists with one atomic per list kind on the running totals (stats[2],
 // stats[3]) and copies them there, coalesced.  Totals beyond the buffers
 // flag ST_LISTS and store nothing (counts 0); the host grows and walks again.
+// SYNC is walk_leaf's loop form: free-running for one round of threads,
+// synchronous for several (the host picks it from its leaf count).
 template <bool SYNC>
 __global__ void __launch_bounds__(128, 10) k_walk_arena(WalkArgs W) {
   __shared__ int s_pre[4][2][33];         // per warp: exclusive prefixes of the far and near counts
